@@ -1,0 +1,298 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle tests and the bench.
+
+This module holds NO arithmetic of the method (no glass field, no blends, no
+right-hand side, no integrator).  It only produces the inputs the method is
+run on: the paper's printed material constants (Table 1), parameter sets
+(Table 2 and the voxel readings of the workloads), sphere packings, initial
+fields and random test fields.  Every random draw comes from numpy's PCG64
+generator with an explicit seed, so the same call gives the same input on any
+machine.
+
+Geometry is produced in voxel units and returned in metres (x, y, z, r) rows:
+cell (i, j, k) has its centre at ((i+1/2)h, (j+1/2)h, (k+1/2)h).  The solid
+fraction used to stop the Boolean packer is a sharp voxel count of points
+inside some sphere; it is a property of the synthetic packing, not of the
+paper's smooth glass field G.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+LIQUID, ICE, GLASS = 0, 1, 2
+
+# Table 1 of the paper (Sec. 2.1): physical properties, SI units.
+TABLE1 = {
+    "rho": (997.0, 917.0, 2500.0),      # kg m^-3      liquid, ice, glass
+    "c": (4180.0, 2050.0, 840.0),       # J kg^-1 K^-1
+    "lambda": (0.6, 2.22, 1.1),         # W m^-1 K^-1
+    "latent": 3.34e5,                   # J kg^-1
+    "T_star": 273.15,                   # K
+    "sigma": 0.033,                     # J m^-2
+    "delta_s": 1.121e6,                 # J m^-3 K^-1 (printed)
+    "mu": 1.0e-4,                       # m s^-1 K^-1
+    "alpha": 3.39782e11,                # s m^-2 (printed)
+}
+
+# Table 2 of the paper (Sec. 3.1): alpha for the "large", "small", "tiny" sigma cases.
+ALPHA_MACRO = {"large": 4.17e6, "small": 1.25e7, "tiny": 3.7e8}
+
+MODEL_FULL, MODEL_TEMP, MODEL_MICRO = 0, 1, 2
+REACT_SIGMAP1P, REACT_GRADP = 0, 1
+PREC_FP64, PREC_FP32 = 0, 1
+
+# Face bits for Dirichlet temperature faces: x-, x+, y-, y+, z-, z+.
+FACE_XM, FACE_XP, FACE_YM, FACE_YP, FACE_ZM, FACE_ZP = 1, 2, 4, 8, 16, 32
+
+
+def default_params(**over) -> dict:
+    """Parameter dictionary with Table 1 materials and the Table 2 limiter values.
+
+    Keys mirror the C-ABI struct ``pf_params``; temperatures are offsets
+    theta = T - T* in kelvin.  ``over`` replaces entries.
+    """
+    p = {
+        "rho": TABLE1["rho"],
+        "c": TABLE1["c"],
+        "lambda": TABLE1["lambda"],
+        "latent": TABLE1["latent"],
+        "mu": TABLE1["mu"],
+        "alpha": TABLE1["alpha"],
+        "xi": 1.0e-3,
+        "xi_G": 1.0e-3,
+        "eps0": 0.05,
+        "eps1": 0.2,
+        "b": 1.0,
+        "gamma": 2.0,
+        "zeta": 2.0,
+        "theta_micro": -0.5,
+        "theta_freeze": -25.0,
+        "theta_thaw": 20.0,
+        "t_freeze": math.inf,
+        "dt_min": 1e-300,
+        "dt_max": math.inf,
+        "dirichlet_faces": 0,
+        "harmonic_mean": 0,
+    }
+    for k, v in over.items():
+        if k not in p:
+            raise KeyError(f"unknown parameter {k!r}")
+        p[k] = v
+    return p
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+# ----------------------------------------------------------------- packings
+def _ball_offsets(r: float):
+    """Integer voxel offsets whose centres lie strictly inside a ball of radius r (voxels)."""
+    R = int(math.ceil(r))
+    ax = np.arange(-R, R + 1)
+    return ax
+
+
+def _stamp(mask: np.ndarray, c, r):
+    """Mark voxels whose centres are inside the sphere (c, r) (voxel units, centre at i+1/2)."""
+    n1, n2, n3 = mask.shape[2], mask.shape[1], mask.shape[0]
+    lo = [max(0, int(math.floor(c[d] - r - 0.5))) for d in range(3)]
+    hi = [min((n1, n2, n3)[d], int(math.ceil(c[d] + r + 0.5)) + 1) for d in range(3)]
+    if any(lo[d] >= hi[d] for d in range(3)):
+        return
+    xs = np.arange(lo[0], hi[0]) + 0.5 - c[0]
+    ys = np.arange(lo[1], hi[1]) + 0.5 - c[1]
+    zs = np.arange(lo[2], hi[2]) + 0.5 - c[2]
+    d2 = zs[:, None, None] ** 2 + ys[None, :, None] ** 2 + xs[None, None, :] ** 2
+    mask[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] |= d2 < r * r
+
+
+def packing_rsa(shape, n_spheres, r_lo, r_hi, seed, max_tries=200000):
+    """Random sequential addition of non-overlapping spheres lying inside the box.
+
+    shape = (n1, n2, n3) cells; radii uniform in [r_lo, r_hi] voxels.
+    Returns an (n, 4) array of (x, y, z, r) in voxel units.
+    """
+    g = rng(seed)
+    n1, n2, n3 = shape
+    out = []
+    tries = 0
+    while len(out) < n_spheres:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("RSA packing did not converge")
+        r = g.uniform(r_lo, r_hi)
+        c = (g.uniform(r, n1 - r), g.uniform(r, n2 - r), g.uniform(r, n3 - r))
+        ok = True
+        for (x, y, z, rr) in out:
+            if (x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2 < (r + rr) ** 2:
+                ok = False
+                break
+        if ok:
+            out.append((c[0], c[1], c[2], r))
+    return np.array(out, dtype=np.float64)
+
+
+def packing_boolean(shape, solid_fraction, radius_sampler, seed, max_spheres=10_000_000):
+    """Overlap-allowed (Boolean) placement until the sharp voxel solid fraction reaches the target.
+
+    Centres are uniform over the box; spheres may cross the walls.
+    radius_sampler(g) draws one radius in voxels.
+    Returns (spheres (n, 4) voxel units, achieved sharp solid fraction).
+    """
+    g = rng(seed)
+    n1, n2, n3 = shape
+    mask = np.zeros((n3, n2, n1), dtype=bool)
+    total = mask.size
+    out = []
+    solid = 0
+    batch = 64
+    while solid < solid_fraction * total:
+        for _ in range(batch):
+            r = float(radius_sampler(g))
+            c = (g.uniform(0, n1), g.uniform(0, n2), g.uniform(0, n3))
+            out.append((c[0], c[1], c[2], r))
+            _stamp(mask, c, r)
+        solid = int(mask.sum())
+        if len(out) > max_spheres:
+            raise RuntimeError("Boolean packing did not reach the target")
+        # refine: finish one by one once close
+        if solid > 0.95 * solid_fraction * total:
+            batch = 1
+    return np.array(out, dtype=np.float64), solid / total
+
+
+def uniform_radius(lo, hi):
+    return lambda g: g.uniform(lo, hi)
+
+
+def lognormal_radius(mean, sigma_ln):
+    """Lognormal radii with the given arithmetic mean (voxels) and log-standard deviation."""
+    mu_ln = math.log(mean) - 0.5 * sigma_ln * sigma_ln
+    return lambda g: g.lognormal(mu_ln, sigma_ln)
+
+
+def sharp_solid_mask(shape, spheres_vox):
+    """Voxel mask (z, y, x) of centres inside any sphere (voxel units)."""
+    n1, n2, n3 = shape
+    mask = np.zeros((n3, n2, n1), dtype=bool)
+    for s in spheres_vox:
+        _stamp(mask, s[:3], s[3])
+    return mask
+
+
+def pore_ball_center(shape, spheres_vox, radius, seed, margin=1.0, max_tries=100000):
+    """First drawn centre whose ball of `radius` keeps `margin` voxels from every sphere and wall."""
+    g = rng(seed)
+    n1, n2, n3 = shape
+    for _ in range(max_tries):
+        c = np.array([g.uniform(radius + margin, n - radius - margin) for n in (n1, n2, n3)])
+        d = np.sqrt(((spheres_vox[:, :3] - c) ** 2).sum(axis=1)) - spheres_vox[:, 3]
+        if len(d) == 0 or d.min() >= radius + margin:
+            return c
+    raise RuntimeError("no pore-space seed position found")
+
+
+# ------------------------------------------------------------ initial fields
+def ball_indicator(shape, center_vox, radius_vox) -> np.ndarray:
+    """Sharp 0/1 field (flattened x fastest) of cell centres strictly inside the ball."""
+    n1, n2, n3 = shape
+    z, y, x = np.meshgrid(np.arange(n3) + 0.5, np.arange(n2) + 0.5, np.arange(n1) + 0.5, indexing="ij")
+    d2 = (x - center_vox[0]) ** 2 + (y - center_vox[1]) ** 2 + (z - center_vox[2]) ** 2
+    return (d2 < radius_vox * radius_vox).astype(np.float64).ravel()
+
+
+def top_slab_indicator(shape, planes) -> np.ndarray:
+    """Sharp 0/1 field equal to 1 on the top `planes` x3-planes (k >= n3 - planes)."""
+    n1, n2, n3 = shape
+    f = np.zeros((n3, n2, n1))
+    f[n3 - planes:] = 1.0
+    return f.ravel()
+
+
+def random_fields(shape, seed, theta_scale=5.0, smooth=2):
+    """Random theta (K), phi in [0,1] and G in [0,1] with a few passes of box smoothing.
+
+    Used for right-hand-side parity on arbitrary states; contains cells in the
+    Sigma-limiter bands, in bulk water/ice and in glass.
+    """
+    g = rng(seed)
+    n1, n2, n3 = shape
+
+    def sm(a):
+        for _ in range(smooth):
+            a = (a + np.roll(a, 1, 0) + np.roll(a, -1, 0) + np.roll(a, 1, 1) + np.roll(a, -1, 1)
+                 + np.roll(a, 1, 2) + np.roll(a, -1, 2)) / 7.0
+        return a
+
+    th = sm(g.standard_normal((n3, n2, n1))) * theta_scale
+    ph = sm(g.uniform(-1.5, 2.5, (n3, n2, n1)))
+    ph = np.clip(ph, 0.0, 1.0)
+    G = np.clip(sm(g.uniform(-1.0, 2.0, (n3, n2, n1))), 0.0, 1.0)
+    return th.ravel().copy(), ph.ravel().copy(), G.ravel().copy()
+
+
+# ----------------------------------------------------------------- workloads
+@dataclass
+class Workload:
+    """A complete seeded input: grid, parameters, geometry and initial state."""
+    name: str
+    shape: tuple
+    h: float
+    model: int
+    reaction: int
+    params: dict
+    spheres: np.ndarray            # (n, 4) metres
+    x3_cap: float                  # nan = no cap
+    theta0: np.ndarray             # flattened, x fastest
+    phi0: np.ndarray
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_cells(self):
+        return self.shape[0] * self.shape[1] * self.shape[2]
+
+
+def micro_32(seed=20240104):
+    """32^3 micro-scale constant-supercooling case: 6 RSA spheres r~U[6,9] voxels, ice ball r=4.
+
+    h = 5e-8 m, xi = h, xi_G = 0.4 h, realistic alpha, dT = 0.5 K, zeta = 2, insulated.
+    """
+    shape = (32, 32, 32)
+    h = 5e-8
+    sv = packing_rsa(shape, 6, 6.0, 9.0, seed)
+    c = pore_ball_center(shape, sv, 4.0, seed + 1)
+    phi0 = ball_indicator(shape, c, 4.0)
+    p = default_params(xi=h, xi_G=0.4 * h, zeta=2.0, theta_micro=-0.5, alpha=TABLE1["alpha"])
+    sp = sv.copy()
+    sp *= h
+    return Workload("micro_32", shape, h, MODEL_MICRO, REACT_SIGMAP1P, p, sp, math.nan,
+                    np.full(phi0.shape, -0.5), phi0,
+                    extra={"fixed_dt": 0.1 * p["alpha"] * h * h, "fixed_steps": 200,
+                           "t_end": 4 * 32 * h / (p["mu"] * 0.5), "tol": 1e-6,
+                           "seed_center_vox": c})
+
+
+def full_bead_case(n, seed, solid=0.60, r_lo=10.0, r_hi=16.0, radius_sampler=None,
+                   h=3e-4, theta_ini=1.0, theta_cold=-5.0, name=None):
+    """Full-model glass-bead case on an n^3 grid (the 256^3 freezing workload and its crops).
+
+    Boolean packing to the sharp solid fraction `solid`, top face x3 = L3 held at
+    theta_cold (Dirichlet), other faces insulated, theta = theta_ini initially,
+    ice seed = the two top x3-planes.  alpha = "large sigma" value of Table 2,
+    xi = h, xi_G = 0.4 h, zeta = 2.
+    """
+    shape = (n, n, n)
+    sampler = radius_sampler or uniform_radius(r_lo, r_hi)
+    sv, frac = packing_boolean(shape, solid, sampler, seed)
+    p = default_params(xi=h, xi_G=0.4 * h, zeta=2.0, alpha=ALPHA_MACRO["large"],
+                       dirichlet_faces=FACE_ZP, theta_freeze=theta_cold, theta_thaw=2.0)
+    sp = sv.copy()
+    sp *= h
+    theta0 = np.full(n ** 3, float(theta_ini))
+    phi0 = top_slab_indicator(shape, 2)
+    return Workload(name or f"full_{n}", shape, h, MODEL_FULL, REACT_SIGMAP1P, p, sp, math.nan,
+                    theta0, phi0, extra={"solid_fraction_sharp": frac, "tol": 1e-6,
+                                         "n_spheres": len(sp)})
