@@ -1,0 +1,350 @@
+"""Benchmark: Runge-Kutta-Merson steps of the full phase-field model on a 256^3 glass-bead packing.
+
+One "step" = one adaptive Merson attempt on the whole grid: five fused stage kernels
+(right-hand side + stage combination), the max-norm error reduction and the device-side
+step control (accept/reject, new dt), i.e. one pass of the whole hot path.
+
+Workload (the paper's macro freezing case scaled to a cube): full heat + Allen-Cahn model,
+SigmaP1-P reaction, binary64, 256^3 cells of h = 0.3 mm, Boolean bead packing with radii
+uniform in [10, 16] voxels to 60% solid, theta = +1 K, top face held at -5 K, other faces
+insulated, ice seed in the two top planes, tolerance 1e-6.  Inputs are seeded and synthetic;
+the working set (about 2 GB) is far larger than the 129 MB L2, so no flush is needed.
+
+Metric: cell-stage updates per second (cells x 5 right-hand-side evaluations per attempt,
+rejected attempts included), summed over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload on its own
+GPU (weak scaling; the single-domain solver has no cross-rank exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2401_01672_gb300 import inputs as I  # noqa: E402
+
+METRIC = "cell-stage updates/s"
+UNIT = "cell-stage/s"
+SEED = 20240105
+N_SIDE = 256
+TOL = 1e-6
+
+# Algorithmic work per cell and Merson stage of the full SigmaP1-P model (binary64).
+# Bytes: the fused per-stage schedule reads/writes 24 field words per field per step plus
+# the glass field once per stage: (2*24 + 5) * 8 B / 5 stages = 84.8 B.
+BYTES_PER_CELL_STAGE_F64 = (2 * 24 + 5) * 8 / 5
+# Binary32-field form: stage buffers 4 B, state 8 B (see the design doc for the per-stage table).
+BYTES_PER_CELL_STAGE_F32 = (2 * 100 + 5 * 4) / 5
+# Floating-point operations per cell-stage of the method as written.
+FLOPS_PER_CELL_STAGE = 96
+
+
+def env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def make_workload():
+    return I.full_bead_case(N_SIDE, SEED, name="full_sigmap1p_256")
+
+
+def cpu_sample(w, seconds=10.0, min_steps=2):
+    """Time the oracle as it stands on a crop of the same workload (single thread)."""
+    import oracle
+    oracle.build()
+    c = (128, 128, 32)
+    off = (64, 64, N_SIDE - c[2])  # top of the vessel: Dirichlet face and ice seed
+    h = w.h
+    lo = np.array(off) * h
+    hi = (np.array(off) + np.array(c)) * h
+    sp = w.spheres
+    # spheres whose terms can reach the crop (beyond r + 40 xi_G they are below 1e-17)
+    reach = sp[:, 3] + 40 * w.params["xi_G"]
+    near = np.all((sp[:, :3] > lo - reach[:, None]) & (sp[:, :3] < hi + reach[:, None]), axis=1)
+    sps = sp[near].copy()
+    sps[:, :3] -= lo
+    o = oracle.Oracle(c, h, w.model, w.reaction, w.params)
+    G = o.glass(sps, w.params["xi_G"])
+    th = np.full(o.N, 1.0)
+    ph = I.top_slab_indicator(c, 2)
+    n, t0 = 0, time.perf_counter()
+    t, dt = 0.0, 0.01
+    while True:
+        th1, ph1, E = o.rkm_step(G, th, ph, t, dt)
+        n += 1
+        el = time.perf_counter() - t0
+        if n >= min_steps and el >= seconds:
+            break
+    cells = c[0] * c[1] * c[2]
+    return {"value": cells * 5 * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} Merson steps on a {c[0]}x{c[1]}x{c[2]} crop (top of the 256^3 workload, "
+                      f"{len(sps)} nearby beads), single thread, {el:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the oracle timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    w = make_workload()
+    per = []
+    for _ in range(args.warmup):
+        cpu_sample(w, seconds=0.0, min_steps=1)
+    t0 = time.perf_counter()
+    res = None
+    for _ in range(args.steps):
+        res = cpu_sample(w, seconds=0.0, min_steps=1)
+        per.append(res["value"])
+    el = time.perf_counter() - t0
+    value = statistics.mean(per)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "grid": [N_SIDE] * 3, "sample": "128x128x32 crop",
+                                            "l2": "inputs larger than L2 not applicable (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": res["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_form(torch, pf, w, precision, steps, warmup, stream):
+    """Device-timed adaptive attempts of one precision form; returns timing and stage profile."""
+    g = pf.Grid(w.shape, w.h, w.model, w.reaction, precision, w.params, stream=stream)
+    g.set_geometry(w.spheres, w.x3_cap)
+    g.set_state(w.theta0, w.phi0, 0.0, 0.01)
+    # warm-up attempts (also reaches the steady step size of the initial transient)
+    g.run_to(math.inf, TOL, warmup)
+    torch.cuda.synchronize()
+    l0 = pf.pf_kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s = g.run_to(math.inf, TOL, steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = pf.pf_kernel_launches() - l0
+    prof = g.profile_stages(3)
+    return g, s, ms, launches, prof
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32-form", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local = env_int("LOCAL_RANK", 0)
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2401_01672_gb300 import pf
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = make_workload()
+    stream = torch.cuda.Stream()
+    peaks, peak_kind = load_peaks()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---------------- timed region: binary64 adaptive attempts
+    g = pf.Grid(w.shape, w.h, w.model, w.reaction, I.PREC_FP64, w.params, stream=stream)
+    g.set_geometry(w.spheres, w.x3_cap)
+    g.set_state(w.theta0, w.phi0, 0.0, 0.01)
+    g.run_to(math.inf, TOL, args.warmup)
+    barrier()
+    l0 = pf.pf_kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        e0.record(stream)
+        s = g.run_to(math.inf, TOL, args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = pf.pf_kernel_launches() - l0
+    attempts = s["n_accepted"] + s["n_rejected"]
+    local_units = w.n_cells * 5 * attempts
+    ms_max = ms
+    units = local_units
+    if dist:
+        tt = torch.tensor([ms, float(local_units)], device="cuda", dtype=torch.float64)
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        ms_max, units = float(mx[0]), float(tt[1])
+    value = units / (ms_max * 1e-3)
+
+    # ---------------- dominant kernel, timed live with CUDA events on the launching stream
+    prof = g.profile_stages(3)
+    stage_names = ["stage1", "stage2", "stage3", "stage4", "stage5", "controller"]
+    top = int(np.argmax(prof[:5]))
+    top_ms = prof[top]
+    flops = FLOPS_PER_CELL_STAGE * w.n_cells
+    fp64_peak_tflops = 152 * 2 * 2 * 2.07e9 / 1e12   # 2 FP64 FMA / clk / SM
+    achieved_tf = flops / (top_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": f"merson_{stage_names[top]}_full_sigmap1p_f64",
+                "achieved": achieved_tf, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved_tf / fp64_peak_tflops, "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (binary64 pipe)",
+                "hbm_achieved_gbs": BYTES_PER_CELL_STAGE_F64 * w.n_cells / (top_ms * 1e-3) / 1e9,
+                "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peak_kind,
+                "stage_ms": dict(zip(stage_names, prof))}
+
+    # ---------------- e2e: host-resident state in pinned memory, copies inside the timed region
+    pin_th = torch.from_numpy(w.theta0.copy()).pin_memory()
+    pin_ph = torch.from_numpy(w.phi0.copy()).pin_memory()
+    g.get_state(pin_th, pin_ph)
+    barrier()
+    e2e_steps = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    e2e_attempts = 0
+    for _ in range(e2e_steps):
+        g.set_state(pin_th, pin_ph, 0.0, s["dt"])
+        r = g.run_to(math.inf, TOL, 1)
+        e2e_attempts += r["n_accepted"] + r["n_rejected"]
+        u = g.unfrozen_fraction()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": w.n_cells * 5 * e2e_attempts / e2e_s * (units / local_units), "unit": UNIT,
+           "h2d_bytes_per_step": 2 * 8 * w.n_cells, "d2h_bytes_per_step": 2 * 136 + 32,
+           "note": "per step: pf_set_state from pinned host theta/phi, one pf_run_to attempt, pf_unfrozen_fraction"}
+    g.close()
+
+    # ---------------- binary32-field form on the same workload
+    forms = {}
+    if not args.no_fp32_form:
+        g32, s32, ms32, l32, prof32 = time_form(torch, pf, w, I.PREC_FP32, args.steps, args.warmup, stream)
+        att32 = s32["n_accepted"] + s32["n_rejected"]
+        top32 = int(np.argmax(prof32[:5]))
+        forms["fp32_fields"] = {
+            "value": w.n_cells * 5 * att32 / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32 / max(att32, 1),
+            "gpu_launches": l32, "dtype": "f32 fields / f64 state",
+            "roofline": {"bound": "hbm", "kernel": f"merson_{stage_names[top32]}_full_sigmap1p_f32",
+                         "achieved": BYTES_PER_CELL_STAGE_F32 * w.n_cells / (prof32[top32] * 1e-3) / 1e9,
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": BYTES_PER_CELL_STAGE_F32 * w.n_cells / (prof32[top32] * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                         "traffic": None, "peak_source": peak_kind,
+                         "stage_ms": dict(zip(stage_names, prof32))}}
+        g32.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_sample(w)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / max(attempts, 1), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": w.name, "grid": list(w.shape), "h_m": w.h, "model": "full",
+                           "reaction": "SigmaP1-P", "beads": int(w.extra["n_spheres"]),
+                           "solid_fraction": round(w.extra["solid_fraction_sharp"], 4), "tol": TOL,
+                           "attempts": attempts, "accepted": s["n_accepted"],
+                           "l2": "inputs larger than L2 (about 2 GB working set)",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk.summary(), "forms": forms, "wall_s_timed": t_wall}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

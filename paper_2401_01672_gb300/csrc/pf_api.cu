@@ -1,0 +1,894 @@
+// C ABI of the GB300 phase-field library: grid lifecycle, geometry, state,
+// Runge-Kutta-Merson driving, unfrozen-water reductions (arXiv 2401.01672).
+#include "../../include/pf.h"
+#include "pf_internal.cuh"
+
+#include <atomic>
+#include <cfloat>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace pfgb;
+
+namespace pfgb {
+static std::atomic<long long> g_launches{0};
+void count_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace pfgb
+
+static thread_local std::string t_create_err;
+
+struct pf_grid {
+    int n1 = 0, n2 = 0, n3 = 0;
+    long long N = 0;
+    double h = 0;
+    int model = 0, rx = 0, prec = 0;
+    pf_params p{};
+    Coefs cf{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int by = 8, zc = 32;
+    double* y_th[2] = {nullptr, nullptr};
+    double* y_ph[2] = {nullptr, nullptr};
+    void* ua_th = nullptr; void* ua_ph = nullptr;
+    void* ub_th = nullptr; void* ub_ph = nullptr;
+    void* k1_th = nullptr; void* k1_ph = nullptr;
+    void* k3_th = nullptr; void* k3_ph = nullptr;
+    void* k4_th = nullptr; void* k4_ph = nullptr;
+    double* G64 = nullptr;
+    float* G32 = nullptr;
+    double* scratch64 = nullptr;
+    void* red = nullptr;
+    size_t red_bytes = 0;
+    Ctrl* dctrl = nullptr;
+    Ctrl* hctrl = nullptr;  // pinned mirror
+    double** ptab = nullptr;  // device table {y_ph[0], y_ph[1], y_th[0], y_th[1]}
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    long long launches = 0;
+    std::vector<void*> allocs;
+    std::string err;
+};
+
+// ------------------------------------------------------------------ helpers
+#define PF_CUDA(g, call)                                                              \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) return fail((g), PF_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static pf_status fail(pf_grid* g, pf_status s, const std::string& msg) {
+    if (g) g->err = msg;
+    else t_create_err = msg;
+    return s;
+}
+
+static bool is_f32(const pf_grid* g) { return g->prec == PF_PREC_FP32_FIELDS; }
+static size_t fbytes(const pf_grid* g) { return is_f32(g) ? sizeof(float) : sizeof(double); }
+static bool has_th(const pf_grid* g) { return g->model != PF_MODEL_MICRO; }
+static bool has_ph(const pf_grid* g) { return g->model != PF_MODEL_TEMP; }
+
+static int blocks_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    if (b > 152LL * 16) b = 152LL * 16;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// ------------------------------------------------------------------ kernels
+__global__ void k_fill(double* p, long long n, double v) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        p[q] = v;
+}
+
+__global__ void k_to_f32(const double* __restrict__ in, float* __restrict__ out, long long n) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        out[q] = (float)in[q];
+}
+
+// Sec. 2.1, G_balls: one block per sphere scatters 1/2 (1 - tanh((|x - x_s| - r_s)/(2 xi_G))) into the
+// cells within r_s + 40 xi_G of its centre by atomicMax on the bit pattern (G >= 0).  Beyond that radius
+// the term is below e^-40 and is skipped.
+__global__ void k_glass_spheres(const double* __restrict__ sp, long long ns, double* G, int n1, int n2, int n3,
+                                double h, double xi_G) {
+    const long long s = blockIdx.x;
+    if (s >= ns) return;
+    const double cx = sp[4 * s], cy = sp[4 * s + 1], cz = sp[4 * s + 2], r = sp[4 * s + 3];
+    const double rc = r + 40.0 * xi_G;
+    int lo[3], hi[3];
+    const double cc[3] = {cx, cy, cz};
+    const int nn[3] = {n1, n2, n3};
+    for (int d = 0; d < 3; ++d) {
+        double a = floor((cc[d] - rc) / h - 0.5), b = ceil((cc[d] + rc) / h - 0.5);
+        lo[d] = (int)fmax(0.0, a);
+        hi[d] = (int)fmin((double)(nn[d] - 1), b);
+    }
+    if (lo[0] > hi[0] || lo[1] > hi[1] || lo[2] > hi[2]) return;
+    const long long bx = hi[0] - lo[0] + 1, byy = hi[1] - lo[1] + 1, bz = hi[2] - lo[2] + 1;
+    const long long nb = bx * byy * bz;
+    const double inv2x = 1.0 / (2.0 * xi_G);
+    unsigned long long* Gb = reinterpret_cast<unsigned long long*>(G);
+    for (long long q = threadIdx.x; q < nb; q += blockDim.x) {
+        const int i = lo[0] + (int)(q % bx);
+        const int j = lo[1] + (int)((q / bx) % byy);
+        const int k = lo[2] + (int)(q / (bx * byy));
+        const double dx = (i + 0.5) * h - cx, dy = (j + 0.5) * h - cy, dz = (k + 0.5) * h - cz;
+        const double dist = sqrt(dx * dx + dy * dy + dz * dz);
+        if (dist - r > 40.0 * xi_G) continue;
+        const double g = 0.5 * (1.0 - tanh((dist - r) * inv2x));
+        if (g > 0.0) atomicMax(&Gb[i + (long long)n1 * (j + (long long)n2 * k)], (unsigned long long)__double_as_longlong(g));
+    }
+}
+
+// Sec. 2.1: G = max(G_balls, 1/2 (1 + tanh((x3 - x3cap)/(2 xi_G))))
+__global__ void k_glass_cap(double* G, int n1, int n2, int n3, double h, double xi_G, double x3cap) {
+    const long long n = (long long)n1 * n2 * n3;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(q / ((long long)n1 * n2));
+        const double z = (k + 0.5) * h;
+        const double g = 0.5 * (1.0 + tanh((z - x3cap) / (2.0 * xi_G)));
+        if (g > G[q]) G[q] = g;
+    }
+}
+
+// Temp model phase field, eq. (explicit-p-dependence-on-T)
+__global__ void k_temp_phi(const double* __restrict__ th, const double* __restrict__ G, double* __restrict__ ph,
+                           long long n, double gamma, double zeta) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        double iw = 1.0 - zeta * G[q];
+        iw = iw > 0.0 ? iw : 0.0;
+        ph[q] = 0.5 * iw * (1.0 - tanh(gamma * th[q]));
+    }
+}
+
+// Step control after stage 5 (one thread).  Accept iff E <= tol (or fixed mode); proposal
+// dt * min(5, 0.8 (tol/E)^(1/5)) capped at dt_max; the next step is shortened to land on
+// t_freeze or t_end.
+__global__ void k_controller(Ctrl* c) {
+    if (threadIdx.x != 0 || blockIdx.x != 0 || c->done) return;
+    const double E = __longlong_as_double((long long)c->err_bits);
+    c->err_bits = 0ULL;
+    c->last_err = E;
+    const bool finite = E <= DBL_MAX;
+    const bool accept = c->fixed || (finite && E <= c->tol);
+    c->accepted = accept;
+    if (!finite && !c->fixed) {
+        c->status = PF_E_NONFINITE;
+        c->done = 1;
+        return;
+    }
+    if (accept) {
+        c->t = c->land ? c->target : c->t + c->dt_step;
+        c->cur ^= 1;
+        c->n_acc++;
+    } else {
+        c->n_rej++;
+    }
+    if (!c->fixed || c->single) {
+        double fac;
+        if (E == 0.0) {
+            fac = 5.0;
+        } else {
+            fac = 0.8 * pow(c->tol / E, 0.2);
+            if (fac > 5.0) fac = 5.0;
+        }
+        double dn = c->dt_step * fac;
+        if (dn > c->dt_max) dn = c->dt_max;
+        c->dt = dn;
+        if (!c->fixed && dn < c->dt_min) {
+            c->status = PF_E_DT_UNDERFLOW;
+            c->done = 1;
+            return;
+        }
+    }
+    if (c->single) return;
+    if (c->t >= c->t_end || c->n_acc + c->n_rej >= c->max_attempts) {
+        c->done = 1;
+        return;
+    }
+    double target = c->t_end;
+    if (c->t < c->t_freeze && c->t_freeze < target) target = c->t_freeze;
+    if (c->t + c->dt >= target) {
+        c->dt_step = target - c->t;
+        c->land = 1;
+        c->target = target;
+    } else {
+        c->dt_step = c->dt;
+        c->land = 0;
+    }
+}
+
+// UWC partial sums over a half-open box; one slot of 4 words per block:
+// [n_water, n_ice] as unsigned 64-bit, [sum (1-G) phi, sum (1-G)] as binary64.
+struct UwcPart { unsigned long long nw, ni; double sn, sd; };
+
+template <int BS>
+__global__ void __launch_bounds__(BS) k_uwc_partial(const double* __restrict__ G, const double* const* yph,
+                                                    const double* const* yth, const Ctrl* ctrl, int temp,
+                                                    double gamma, double zeta, int n1, int n2, int i0, int i1,
+                                                    int j0, int j1, int k0, int k1, UwcPart* parts) {
+    const int cur = ctrl->cur;
+    const double* ph = temp ? nullptr : yph[cur];
+    const double* th = temp ? yth[cur] : nullptr;
+    const long long bx = i1 - i0, byy = j1 - j0, bz = k1 - k0;
+    const long long n = bx * byy * bz;
+    unsigned long long nw = 0, ni = 0;
+    double sn = 0.0, sd = 0.0;
+    for (long long q = blockIdx.x * (long long)BS + threadIdx.x; q < n; q += (long long)gridDim.x * BS) {
+        const int i = i0 + (int)(q % bx), j = j0 + (int)((q / bx) % byy), k = k0 + (int)(q / (bx * byy));
+        const long long id = i + (long long)n1 * (j + (long long)n2 * k);
+        const double g = G[id];
+        double p;
+        if (temp) {
+            double iw = 1.0 - zeta * g;
+            iw = iw > 0.0 ? iw : 0.0;
+            p = 0.5 * iw * (1.0 - tanh(gamma * th[id]));
+        } else {
+            p = ph[id];
+        }
+        if (g < 0.5) {
+            ++nw;
+            if (p > 0.5) ++ni;
+        }
+        sn += (1.0 - g) * p;
+        sd += (1.0 - g);
+    }
+    __shared__ UwcPart sp[BS];
+    sp[threadIdx.x] = {nw, ni, sn, sd};
+    __syncthreads();
+    for (int s = BS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sp[threadIdx.x].nw += sp[threadIdx.x + s].nw;
+            sp[threadIdx.x].ni += sp[threadIdx.x + s].ni;
+            sp[threadIdx.x].sn += sp[threadIdx.x + s].sn;
+            sp[threadIdx.x].sd += sp[threadIdx.x + s].sd;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) parts[blockIdx.x] = sp[0];
+}
+
+// Fixed-order final sum of the per-block partials (deterministic binary64 result).
+__global__ void k_uwc_final(UwcPart* parts, int nparts, UwcPart* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    UwcPart acc = {0, 0, 0.0, 0.0};
+    for (int b = 0; b < nparts; ++b) {
+        acc.nw += parts[b].nw;
+        acc.ni += parts[b].ni;
+        acc.sn += parts[b].sn;
+        acc.sd += parts[b].sd;
+    }
+    *out = acc;
+}
+
+// max |v| over n values of type T -> per-block partial maxima (binary64), then a final pass.
+template <typename T, int BS>
+__global__ void __launch_bounds__(BS) k_maxabs_partial(const T* __restrict__ v, long long n, double* parts) {
+    double m = 0.0;
+    for (long long q = blockIdx.x * (long long)BS + threadIdx.x; q < n; q += (long long)gridDim.x * BS) {
+        double a = fabs((double)v[q]);
+        if (!(a <= DBL_MAX)) a = INFINITY;
+        m = a > m ? a : m;
+    }
+    __shared__ double s[BS];
+    s[threadIdx.x] = m;
+    __syncthreads();
+    for (int k = BS / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) s[threadIdx.x] = fmax(s[threadIdx.x], s[threadIdx.x + k]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) parts[blockIdx.x] = s[0];
+}
+
+__global__ void k_max_final(const double* parts, int n, double* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double m = 0.0;
+    for (int b = 0; b < n; ++b) m = parts[b] > m ? parts[b] : m;
+    *out = m;
+}
+
+// ------------------------------------------------------------------ stage dispatch
+template <typename T>
+static StageArgs<T> make_args(pf_grid* g) {
+    StageArgs<T> a{};
+    a.cf = g->cf;
+    a.ctrl = g->dctrl;
+    for (int b = 0; b < 2; ++b) {
+        a.y_th[b] = g->y_th[b];
+        a.y_ph[b] = g->y_ph[b];
+        a.yo_th[b] = g->y_th[b];
+        a.yo_ph[b] = g->y_ph[b];
+    }
+    a.ua_th = (T*)g->ua_th; a.ua_ph = (T*)g->ua_ph;
+    a.ub_th = (T*)g->ub_th; a.ub_ph = (T*)g->ub_ph;
+    a.k1_th = (T*)g->k1_th; a.k1_ph = (T*)g->k1_ph;
+    a.k3_th = (T*)g->k3_th; a.k3_ph = (T*)g->k3_ph;
+    a.k4_th = (T*)g->k4_th; a.k4_ph = (T*)g->k4_ph;
+    if constexpr (std::is_same<T, float>::value) a.G = g->G32;
+    else a.G = g->G64;
+    a.zc = g->zc;
+    return a;
+}
+
+static cudaError_t launch_stage(pf_grid* g, int stage, cudaStream_t s) {
+    g->launches++;
+    if (is_f32(g)) return launch_stage_f32(g->model, g->rx, stage, make_args<float>(g), g->by, s);
+    return launch_stage_f64(g->model, g->rx, stage, make_args<double>(g), g->by, s);
+}
+
+// S1..S5 + controller on stream s
+static cudaError_t enqueue_attempt(pf_grid* g, cudaStream_t s) {
+    for (int st = 1; st <= 5; ++st) {
+        cudaError_t e = launch_stage(g, st, s);
+        if (e != cudaSuccess) return e;
+    }
+    k_controller<<<1, 32, 0, s>>>(g->dctrl);
+    count_launch();
+    g->launches++;
+    return cudaGetLastError();
+}
+
+static void free_graph(pf_grid* g) {
+    if (g->graph) cudaGraphExecDestroy(g->graph);
+    g->graph = nullptr;
+    g->graph_steps = 0;
+}
+
+// Capture `steps` attempts into one executable graph (replayed by pf_run_to / pf_run_fixed).
+static pf_status build_graph(pf_grid* g, int steps) {
+    free_graph(g);
+    cudaGraph_t graph = nullptr;
+    PF_CUDA(g, cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+    long long before = g->launches;
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < steps && e == cudaSuccess; ++s) e = enqueue_attempt(g, g->cap_stream);
+    cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &graph);
+    // launches made during capture are only recorded, not executed
+    g->launches = before;
+    pfgb::g_launches.fetch_sub((long long)steps * 6, std::memory_order_relaxed);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(g, PF_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaError_t e3 = cudaGraphInstantiate(&g->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e3 != cudaSuccess) {
+        g->graph = nullptr;
+        return fail(g, PF_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e3));
+    }
+    g->graph_steps = steps;
+    return PF_OK;
+}
+
+static pf_status sync_ctrl_to_host(pf_grid* g) {
+    PF_CUDA(g, cudaMemcpyAsync(g->hctrl, g->dctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, g->stream));
+    PF_CUDA(g, cudaStreamSynchronize(g->stream));
+    return PF_OK;
+}
+
+static pf_status push_ctrl(pf_grid* g) {
+    PF_CUDA(g, cudaMemcpyAsync(g->dctrl, g->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, g->stream));
+    return PF_OK;
+}
+
+// ------------------------------------------------------------------ ABI
+extern "C" {
+
+const char* pf_last_error(const pf_grid* g) { return g ? g->err.c_str() : t_create_err.c_str(); }
+
+long long pf_kernel_launches(void) { return pfgb::g_launches.load(); }
+
+static void destroy_impl(pf_grid* g) {
+    free_graph(g);
+    for (void* p : g->allocs) cudaFree(p);
+    if (g->hctrl) cudaFreeHost(g->hctrl);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    delete g;
+}
+
+pf_status pf_destroy_grid(pf_grid* g) {
+    if (!g) return PF_OK;
+    cudaStreamSynchronize(g->stream);
+    destroy_impl(g);
+    return PF_OK;
+}
+
+pf_status pf_create_grid(int n1, int n2, int n3, double h, int model, int reaction, int precision,
+                         const pf_params* p, void* stream, pf_grid** out) {
+    if (!out) return fail(nullptr, PF_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!p) return fail(nullptr, PF_E_INVALID, "params is NULL");
+    if (n1 < 1 || n2 < 1 || n3 < 1) return fail(nullptr, PF_E_INVALID, "grid sizes must be >= 1");
+    if ((long long)n1 * n2 * n3 > (1LL << 36)) return fail(nullptr, PF_E_INVALID, "grid too large");
+    if (!(h > 0.0)) return fail(nullptr, PF_E_INVALID, "h must be > 0");
+    if (model < 0 || model > 2) return fail(nullptr, PF_E_INVALID, "unknown model");
+    if (reaction < 0 || reaction > 1) return fail(nullptr, PF_E_INVALID, "unknown reaction");
+    if (precision < 0 || precision > 1) return fail(nullptr, PF_E_INVALID, "unknown precision");
+    if (model != PF_MODEL_TEMP && (!(p->alpha > 0) || !(p->xi > 0) || !(p->eps1 > p->eps0)))
+        return fail(nullptr, PF_E_INVALID, "alpha, xi must be > 0 and eps1 > eps0");
+    if (!(p->zeta >= 0)) return fail(nullptr, PF_E_INVALID, "zeta must be >= 0");
+    if (model != PF_MODEL_MICRO)
+        for (int m = 0; m < 3; ++m)
+            if (!(p->rho[m] > 0) || !(p->c[m] > 0) || !(p->lambda[m] >= 0))
+                return fail(nullptr, PF_E_INVALID, "rho, c must be > 0 and lambda >= 0");
+
+    pf_grid* g = new pf_grid();
+    g->n1 = n1; g->n2 = n2; g->n3 = n3;
+    g->N = (long long)n1 * n2 * n3;
+    g->h = h;
+    g->model = model; g->rx = reaction; g->prec = precision;
+    g->p = *p;
+    g->stream = (cudaStream_t)stream;
+    Coefs& c = g->cf;
+    c.n1 = n1; c.n2 = n2; c.n3 = n3;
+    c.dirichlet = (model == PF_MODEL_MICRO) ? 0 : (p->dirichlet_faces & 63);
+    c.harmonic = p->harmonic_mean ? 1 : 0;
+    c.inv_h2 = 1.0 / (h * h);
+    c.half_inv_h2 = 0.5 / (h * h);
+    for (int m = 0; m < 3; ++m) { c.lam[m] = p->lambda[m]; c.rho[m] = p->rho[m]; c.cap[m] = p->c[m]; }
+    c.latent = p->latent;
+    c.xi2 = p->xi * p->xi;
+    c.inv_axi2 = (p->alpha > 0 && p->xi > 0) ? 1.0 / (p->alpha * p->xi * p->xi) : 0.0;
+    c.ksig = 0.5 * p->xi * p->b * p->mu * p->alpha;
+    c.kgrad = p->xi * p->xi * p->mu * p->alpha / (2.0 * h);
+    c.eps0 = p->eps0; c.eps1 = p->eps1;
+    c.inv_de = (p->eps1 > p->eps0) ? 1.0 / (p->eps1 - p->eps0) : 0.0;
+    c.gamma = p->gamma; c.zeta = p->zeta;
+    c.theta_micro = p->theta_micro;
+    c.theta_freeze = p->theta_freeze; c.theta_thaw = p->theta_thaw; c.t_freeze = p->t_freeze;
+
+    auto alloc = [&](size_t bytes) -> void* {
+        void* q = nullptr;
+        if (cudaMalloc(&q, bytes) != cudaSuccess) return nullptr;
+        g->allocs.push_back(q);
+        return q;
+    };
+    const size_t nd = sizeof(double) * g->N, nf = fbytes(g) * g->N;
+    bool ok = true;
+    auto A = [&](size_t b) { void* q = alloc(b); ok = ok && q; return q; };
+    if (has_th(g)) {
+        g->y_th[0] = (double*)A(nd); g->y_th[1] = (double*)A(nd);
+        g->ua_th = A(nf); g->ub_th = A(nf); g->k1_th = A(nf); g->k3_th = A(nf); g->k4_th = A(nf);
+    }
+    if (has_ph(g)) {
+        g->y_ph[0] = (double*)A(nd); g->y_ph[1] = (double*)A(nd);
+        g->ua_ph = A(nf); g->ub_ph = A(nf); g->k1_ph = A(nf); g->k3_ph = A(nf); g->k4_ph = A(nf);
+    }
+    g->G64 = (double*)A(nd);
+    if (is_f32(g)) g->G32 = (float*)A(sizeof(float) * g->N);
+    g->scratch64 = (double*)A(nd);
+    g->red_bytes = sizeof(UwcPart) * (152 * 16 + 2);
+    g->red = A(g->red_bytes);
+    g->dctrl = (Ctrl*)A(sizeof(Ctrl));
+    g->ptab = (double**)A(4 * sizeof(double*));
+    cudaGetLastError();
+    if (!ok) {
+        destroy_impl(g);
+        return fail(nullptr, PF_E_OOM, "device allocation failed");
+    }
+    if (cudaMallocHost((void**)&g->hctrl, sizeof(Ctrl)) != cudaSuccess) {
+        cudaGetLastError();
+        destroy_impl(g);
+        return fail(nullptr, PF_E_OOM, "pinned allocation failed");
+    }
+    if (cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        destroy_impl(g);
+        return fail(nullptr, PF_E_CUDA, "stream creation failed");
+    }
+    // default state: all water, theta = 0, phi = 0, t = 0
+    double* h_tab[4] = {g->y_ph[0], g->y_ph[1], g->y_th[0], g->y_th[1]};
+    cudaError_t e = cudaMemcpy(g->ptab, h_tab, sizeof(h_tab), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->dctrl, 0, sizeof(Ctrl), g->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->G64, 0, nd, g->stream);
+    if (e == cudaSuccess && g->G32) e = cudaMemsetAsync(g->G32, 0, sizeof(float) * g->N, g->stream);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        if (g->y_th[b]) e = cudaMemsetAsync(g->y_th[b], 0, nd, g->stream);
+        if (e == cudaSuccess && g->y_ph[b]) e = cudaMemsetAsync(g->y_ph[b], 0, nd, g->stream);
+    }
+    if (e != cudaSuccess) {
+        destroy_impl(g);
+        return fail(nullptr, PF_E_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
+    }
+    std::memset(g->hctrl, 0, sizeof(Ctrl));
+    g->hctrl->dt = std::isfinite(p->dt_max) ? p->dt_max : 1e-3;
+    g->hctrl->t_freeze = p->t_freeze;
+    g->hctrl->dt_min = p->dt_min;
+    g->hctrl->dt_max = p->dt_max;
+    if (push_ctrl(g) != PF_OK || cudaStreamSynchronize(g->stream) != cudaSuccess) {
+        cudaGetLastError();
+        destroy_impl(g);
+        return fail(nullptr, PF_E_CUDA, "initialisation failed");
+    }
+    *out = g;
+    return PF_OK;
+}
+
+static pf_status refresh_g32(pf_grid* g) {
+    if (!g->G32) return PF_OK;
+    k_to_f32<<<blocks_for(g->N, 256), 256, 0, g->stream>>>(g->G64, g->G32, g->N);
+    count_launch();
+    PF_CUDA(g, cudaGetLastError());
+    return PF_OK;
+}
+
+pf_status pf_set_geometry(pf_grid* g, const double* spheres, long long n, double x3_cap) {
+    if (!g) return fail(nullptr, PF_E_INVALID, "grid is NULL");
+    if (n < 0 || (n > 0 && !spheres)) return fail(g, PF_E_INVALID, "bad sphere list");
+    if (!(g->p.xi_G > 0)) return fail(g, PF_E_INVALID, "xi_G must be > 0");
+    for (long long s = 0; s < n; ++s) {
+        for (int d = 0; d < 4; ++d)
+            if (!std::isfinite(spheres[4 * s + d])) return fail(g, PF_E_INVALID, "non-finite sphere");
+        if (!(spheres[4 * s + 3] > 0)) return fail(g, PF_E_INVALID, "sphere radius must be > 0");
+    }
+    PF_CUDA(g, cudaMemsetAsync(g->G64, 0, sizeof(double) * g->N, g->stream));
+    if (n > 0) {
+        double* dsp = nullptr;
+        PF_CUDA(g, cudaMalloc(&dsp, sizeof(double) * 4 * n));
+        cudaError_t e = cudaMemcpyAsync(dsp, spheres, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, g->stream);
+        if (e == cudaSuccess) {
+            const long long chunk = 1LL << 30;
+            for (long long s0 = 0; s0 < n && e == cudaSuccess; s0 += chunk) {
+                long long cnt = n - s0 < chunk ? n - s0 : chunk;
+                k_glass_spheres<<<(unsigned)cnt, 256, 0, g->stream>>>(dsp + 4 * s0, cnt, g->G64, g->n1, g->n2, g->n3,
+                                                                     g->h, g->p.xi_G);
+                count_launch();
+                e = cudaGetLastError();
+            }
+        }
+        cudaError_t e2 = cudaStreamSynchronize(g->stream);
+        cudaFree(dsp);
+        if (e != cudaSuccess || e2 != cudaSuccess)
+            return fail(g, PF_E_CUDA, std::string("glass field: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    if (!std::isnan(x3_cap)) {
+        k_glass_cap<<<blocks_for(g->N, 256), 256, 0, g->stream>>>(g->G64, g->n1, g->n2, g->n3, g->h, g->p.xi_G, x3_cap);
+        count_launch();
+        PF_CUDA(g, cudaGetLastError());
+    }
+    pf_status s = refresh_g32(g);
+    if (s != PF_OK) return s;
+    PF_CUDA(g, cudaStreamSynchronize(g->stream));
+    return PF_OK;
+}
+
+pf_status pf_set_glass(pf_grid* g, const double* G) {
+    if (!g) return fail(nullptr, PF_E_INVALID, "grid is NULL");
+    if (!G) return fail(g, PF_E_INVALID, "G is NULL");
+    PF_CUDA(g, cudaMemcpyAsync(g->G64, G, sizeof(double) * g->N, cudaMemcpyHostToDevice, g->stream));
+    pf_status s = refresh_g32(g);
+    if (s != PF_OK) return s;
+    PF_CUDA(g, cudaStreamSynchronize(g->stream));
+    return PF_OK;
+}
+
+pf_status pf_get_glass(pf_grid* g, double* G) {
+    if (!g) return fail(nullptr, PF_E_INVALID, "grid is NULL");
+    if (!G) return fail(g, PF_E_INVALID, "G is NULL");
+    PF_CUDA(g, cudaMemcpyAsync(G, g->G64, sizeof(double) * g->N, cudaMemcpyDeviceToHost, g->stream));
+    PF_CUDA(g, cudaStreamSynchronize(g->stream));
+    return PF_OK;
+}
+
+pf_status pf_set_state(pf_grid* g, const double* theta, const double* phi, double t, double dt) {
+    if (!g) return fail(nullptr, PF_E_INVALID, "grid is NULL");
+    if (has_th(g) && !theta) return fail(g, PF_E_INVALID, "theta is NULL");
+    if (has_ph(g) && !phi) return fail(g, PF_E_INVALID, "phi is NULL");
+    if (!std::isfinite(t) || !(dt > 0)) return fail(g, PF_E_INVALID, "t must be finite and dt > 0");
+    PF_CUDA(g, cudaStreamSynchronize(g->stream));
+    if (has_th(g)) PF_CUDA(g, cudaMemcpyAsync(g->y_th[0], theta, sizeof(double) * g->N, cudaMemcpyHostToDevice, g->stream));
+    if (has_ph(g)) PF_CUDA(g, cudaMemcpyAsync(g->y_ph[0], phi, sizeof(double) * g->N, cudaMemcpyHostToDevice, g->stream));
+    Ctrl* c = g->hctrl;
+    c->t = t;
+    c->dt = dt;
+    c->cur = 0;
+    c->err_bits = 0;
+    c->done = 0;
+    c->status = 0;
+    c->last_err = 0;
+    pf_status s = push_ctrl(g);
+    if (s != PF_OK) return s;
+    PF_CUDA(g, cudaStreamSynchronize(g->stream));
+    return PF_OK;
+}
+
+pf_status pf_get_state(pf_grid* g, double* theta, double* phi, double* t, double* dt) {
+    if (!g) return fail(nullptr, PF_E_INVALID, "grid is NULL");
+    pf_status s = sync_ctrl_to_host(g);
+    if (s != PF_OK) return s;
+    const int cur = g->hctrl->cur;
+    if (theta) {
+        if (has_th(g)) {
+            PF_CUDA(g, cudaMemcpyAsync(theta, g->y_th[cur], sizeof(double) * g->N, cudaMemcpyDeviceToHost, g->stream));
+        } else {
+            for (long long q = 0; q < g->N; ++q) theta[q] = g->p.theta_micro;
+        }
+    }
+    if (phi) {
+        if (has_ph(g)) {
+            PF_CUDA(g, cudaMemcpyAsync(phi, g->y_ph[cur], sizeof(double) * g->N, cudaMemcpyDeviceToHost, g->stream));
+        } else {
+            k_temp_phi<<<blocks_for(g->N, 256), 256, 0, g->stream>>>(g->y_th[cur], g->G64, g->scratch64, g->N,
+                                                                      g->p.gamma, g->p.zeta);
+            count_launch();
+            PF_CUDA(g, cudaGetLastError());
+            PF_CUDA(g, cudaMemcpyAsync(phi, g->scratch64, sizeof(double) * g->N, cudaMemcpyDeviceToHost, g->stream));
+        }
+    }
+    PF_CUDA(g, cudaStreamSynchronize(g->stream));
+    if (t) *t = g->hctrl->t;
+    if (dt) *dt = g->hctrl->dt;
+    return PF_OK;
+}
+
+pf_status pf_rhs(pf_grid* g, double t, const void* theta_in, const void* phi_in, void* dtheta_out, void* dphi_out) {
+    if (!g) return fail(nullptr, PF_E_INVALID, "grid is NULL");
+    if (has_th(g) && !theta_in) return fail(g, PF_E_INVALID, "theta_in is NULL");
+    if (has_ph(g) && !phi_in) return fail(g, PF_E_INVALID, "phi_in is NULL");
+    if (!std::isfinite(t)) return fail(g, PF_E_INVALID, "t must be finite");
+    cudaError_t e;
+    if (is_f32(g)) {
+        StageArgs<float> a = make_args<float>(g);
+        a.in_th = (const float*)theta_in; a.in_ph = (const float*)phi_in;
+        a.out_th = (float*)dtheta_out; a.out_ph = (float*)dphi_out;
+        a.t_rhs = t;
+        e = launch_stage_f32(g->model, g->rx, 0, a, g->by, g->stream);
+    } else {
+        StageArgs<double> a = make_args<double>(g);
+        a.in_th = (const double*)theta_in; a.in_ph = (const double*)phi_in;
+        a.out_th = (double*)dtheta_out; a.out_ph = (double*)dphi_out;
+        a.t_rhs = t;
+        e = launch_stage_f64(g->model, g->rx, 0, a, g->by, g->stream);
+    }
+    g->launches++;
+    if (e != cudaSuccess) return fail(g, PF_E_CUDA, std::string("rhs launch: ") + cudaGetErrorString(e));
+    // the micro model integrates no temperature: dtheta = 0; Temp has dphi from the kernel
+    if (!has_th(g) && dtheta_out) PF_CUDA(g, cudaMemsetAsync(dtheta_out, 0, fbytes(g) * g->N, g->stream));
+    return PF_OK;
+}
+
+pf_status pf_rkm_step(pf_grid* g, double* dt_inout, double tol, int force_accept, int* accepted, double* err) {
+    if (!g) return fail(nullptr, PF_E_INVALID, "grid is NULL");
+    if (!dt_inout || !(*dt_inout > 0) || !std::isfinite(*dt_inout)) return fail(g, PF_E_INVALID, "dt must be > 0");
+    if (!force_accept && !(tol > 0)) return fail(g, PF_E_INVALID, "tol must be > 0");
+    pf_status s = sync_ctrl_to_host(g);
+    if (s != PF_OK) return s;
+    Ctrl* c = g->hctrl;
+    c->dt_step = *dt_inout;
+    c->dt = *dt_inout;
+    c->land = 0;
+    c->done = 0;
+    c->status = 0;
+    c->fixed = force_accept ? 1 : 0;
+    c->single = 1;
+    c->tol = tol;
+    c->n_acc = c->n_rej = 0;
+    c->err_bits = 0;
+    s = push_ctrl(g);
+    if (s != PF_OK) return s;
+    PF_CUDA(g, enqueue_attempt(g, g->stream));
+    s = sync_ctrl_to_host(g);
+    if (s != PF_OK) return s;
+    if (accepted) *accepted = c->accepted;
+    if (err) *err = c->last_err;
+    *dt_inout = c->dt;
+    if (c->status == PF_E_NONFINITE) return fail(g, PF_E_NONFINITE, "non-finite error estimate");
+    return PF_OK;
+}
+
+static pf_status run_loop(pf_grid* g, pf_run_stats* stats) {
+    const int steps_per_graph = 16;
+    if (!g->graph || g->graph_steps != steps_per_graph) {
+        pf_status s = build_graph(g, steps_per_graph);
+        if (s != PF_OK) return s;
+    }
+    long long launched = 0;
+    pf_status s = push_ctrl(g);
+    if (s != PF_OK) return s;
+    for (;;) {
+        PF_CUDA(g, cudaGraphLaunch(g->graph, g->stream));
+        launched += 6LL * steps_per_graph;
+        s = sync_ctrl_to_host(g);
+        if (s != PF_OK) return s;
+        if (g->hctrl->done) break;
+    }
+    count_launch(launched);
+    g->launches += launched;
+    const Ctrl* c = g->hctrl;
+    if (stats) {
+        stats->n_accepted = c->n_acc;
+        stats->n_rejected = c->n_rej;
+        stats->t = c->t;
+        stats->dt = c->dt;
+        stats->last_err = c->last_err;
+        stats->launches = launched;
+    }
+    if (c->status == PF_E_DT_UNDERFLOW) return fail(g, PF_E_DT_UNDERFLOW, "step size fell below dt_min");
+    if (c->status == PF_E_NONFINITE) return fail(g, PF_E_NONFINITE, "non-finite error estimate");
+    return PF_OK;
+}
+
+static void first_step(Ctrl* c) {
+    double target = c->t_end;
+    if (c->t < c->t_freeze && c->t_freeze < target) target = c->t_freeze;
+    if (c->t + c->dt >= target) {
+        c->dt_step = target - c->t;
+        c->land = 1;
+        c->target = target;
+    } else {
+        c->dt_step = c->dt;
+        c->land = 0;
+    }
+}
+
+pf_status pf_run_to(pf_grid* g, double t_end, double tol, long long max_steps, pf_run_stats* stats) {
+    if (!g) return fail(nullptr, PF_E_INVALID, "grid is NULL");
+    if (!(tol > 0) || std::isnan(t_end)) return fail(g, PF_E_INVALID, "tol must be > 0 and t_end a number");
+    pf_status s = sync_ctrl_to_host(g);
+    if (s != PF_OK) return s;
+    Ctrl* c = g->hctrl;
+    c->t_end = t_end;
+    c->tol = tol;
+    c->fixed = 0;
+    c->single = 0;
+    c->max_attempts = max_steps;
+    c->n_acc = c->n_rej = 0;
+    c->status = 0;
+    c->err_bits = 0;
+    if (!(c->t < t_end) || max_steps <= 0) {
+        if (stats) *stats = {0, 0, c->t, c->dt, c->last_err, 0};
+        return PF_OK;
+    }
+    c->done = 0;
+    first_step(c);
+    return run_loop(g, stats);
+}
+
+pf_status pf_run_fixed(pf_grid* g, long long n_steps, double dt, pf_run_stats* stats) {
+    if (!g) return fail(nullptr, PF_E_INVALID, "grid is NULL");
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(g, PF_E_INVALID, "dt must be > 0");
+    pf_status s = sync_ctrl_to_host(g);
+    if (s != PF_OK) return s;
+    Ctrl* c = g->hctrl;
+    c->t_end = INFINITY;
+    c->tol = 0.0;
+    c->fixed = 1;
+    c->single = 0;
+    c->max_attempts = n_steps;
+    c->n_acc = c->n_rej = 0;
+    c->status = 0;
+    c->err_bits = 0;
+    c->dt = dt;
+    if (n_steps <= 0) {
+        if (stats) *stats = {0, 0, c->t, c->dt, c->last_err, 0};
+        return PF_OK;
+    }
+    c->done = 0;
+    first_step(c);
+    return run_loop(g, stats);
+}
+
+pf_status pf_unfrozen_fraction(pf_grid* g, const int* region, double* uwc, long long* n_ice, long long* n_water,
+                               double* smooth) {
+    if (!g) return fail(nullptr, PF_E_INVALID, "grid is NULL");
+    int r[6] = {0, g->n1, 0, g->n2, 0, g->n3};
+    if (region) {
+        std::memcpy(r, region, sizeof(r));
+        if (r[0] < 0 || r[1] > g->n1 || r[2] < 0 || r[3] > g->n2 || r[4] < 0 || r[5] > g->n3 || r[0] > r[1] ||
+            r[2] > r[3] || r[4] > r[5])
+            return fail(g, PF_E_INVALID, "region outside the grid");
+    }
+    const long long n = (long long)(r[1] - r[0]) * (r[3] - r[2]) * (r[5] - r[4]);
+    const int nb = n > 0 ? blocks_for(n, 256) : 1;
+    UwcPart* parts = (UwcPart*)g->red;
+    UwcPart* res = parts + (152 * 16);
+    double** tab = g->ptab;  // the kernel picks the current state buffer from ctrl->cur
+    k_uwc_partial<256><<<nb, 256, 0, g->stream>>>(g->G64, (const double* const*)tab, (const double* const*)(tab + 2),
+                                                  g->dctrl, g->model == PF_MODEL_TEMP, g->p.gamma, g->p.zeta, g->n1,
+                                                  g->n2, r[0], r[1], r[2], r[3], r[4], r[5], parts);
+    k_uwc_final<<<1, 32, 0, g->stream>>>(parts, nb, res);
+    count_launch(2);
+    g->launches += 2;
+    PF_CUDA(g, cudaGetLastError());
+    UwcPart hres;
+    PF_CUDA(g, cudaMemcpyAsync(&hres, res, sizeof(UwcPart), cudaMemcpyDeviceToHost, g->stream));
+    PF_CUDA(g, cudaStreamSynchronize(g->stream));
+    if (n_ice) *n_ice = (long long)hres.ni;
+    if (n_water) *n_water = (long long)hres.nw;
+    if (uwc) *uwc = hres.nw ? 1.0 - (double)hres.ni / (double)hres.nw : NAN;
+    if (smooth) *smooth = hres.sd != 0.0 ? 1.0 - hres.sn / hres.sd : NAN;
+    return PF_OK;
+}
+
+pf_status pf_profile_stages(pf_grid* g, int n_attempts, double* stage_ms) {
+    if (!g) return fail(nullptr, PF_E_INVALID, "grid is NULL");
+    if (n_attempts < 1 || !stage_ms) return fail(g, PF_E_INVALID, "n_attempts >= 1 and stage_ms required");
+    pf_status s = sync_ctrl_to_host(g);
+    if (s != PF_OK) return s;
+    Ctrl* c = g->hctrl;
+    c->fixed = 1;
+    c->single = 1;
+    c->dt_step = c->dt;
+    c->land = 0;
+    c->done = 0;
+    c->status = 0;
+    c->err_bits = 0;
+    s = push_ctrl(g);
+    if (s != PF_OK) return s;
+    cudaEvent_t ev[7];
+    for (int q = 0; q < 7; ++q) PF_CUDA(g, cudaEventCreate(&ev[q]));
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    cudaError_t e = cudaSuccess;
+    for (int a = 0; a < n_attempts && e == cudaSuccess; ++a) {
+        e = cudaEventRecord(ev[0], g->stream);
+        for (int st = 1; st <= 5 && e == cudaSuccess; ++st) {
+            e = launch_stage(g, st, g->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[st], g->stream);
+        }
+        if (e == cudaSuccess) {
+            k_controller<<<1, 32, 0, g->stream>>>(g->dctrl);
+            count_launch();
+            g->launches++;
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev[6], g->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[6]);
+        for (int q = 0; q < 6 && e == cudaSuccess; ++q) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, ev[q], ev[q + 1]);
+            acc[q] += ms;
+        }
+    }
+    for (int q = 0; q < 7; ++q) cudaEventDestroy(ev[q]);
+    if (e != cudaSuccess) return fail(g, PF_E_CUDA, std::string("profile: ") + cudaGetErrorString(e));
+    for (int q = 0; q < 6; ++q) stage_ms[q] = acc[q] / n_attempts;
+    return sync_ctrl_to_host(g);
+}
+
+pf_status pf_max_phase_rate(pf_grid* g, double* max_rate) {
+    if (!g) return fail(nullptr, PF_E_INVALID, "grid is NULL");
+    if (!max_rate) return fail(g, PF_E_INVALID, "max_rate is NULL");
+    pf_status s = sync_ctrl_to_host(g);
+    if (s != PF_OK) return s;
+    const int cur = g->hctrl->cur;
+    const double t = g->hctrl->t;
+    cudaError_t e;
+    const int nb = blocks_for(g->N, 256);
+    double* parts = (double*)g->red;
+    double* res = parts + 152 * 16;
+    if (is_f32(g)) {
+        // binary32 copies of the binary64 state feed the binary32 right-hand side
+        if (has_th(g)) { k_to_f32<<<nb, 256, 0, g->stream>>>(g->y_th[cur], (float*)g->ua_th, g->N); count_launch(); }
+        if (has_ph(g)) { k_to_f32<<<nb, 256, 0, g->stream>>>(g->y_ph[cur], (float*)g->ua_ph, g->N); count_launch(); }
+        StageArgs<float> a = make_args<float>(g);
+        a.in_th = (const float*)g->ua_th; a.in_ph = (const float*)g->ua_ph;
+        a.out_th = nullptr; a.out_ph = (float*)g->k1_ph;
+        if (!has_ph(g)) a.out_ph = (float*)g->k1_th;  // Temp: dphi goes to the theta slot
+        a.t_rhs = t;
+        e = launch_stage_f32(g->model, g->rx, 0, a, g->by, g->stream);
+        if (e == cudaSuccess) {
+            k_maxabs_partial<float, 256><<<nb, 256, 0, g->stream>>>((const float*)a.out_ph, g->N, parts);
+            count_launch();
+        }
+    } else {
+        StageArgs<double> a = make_args<double>(g);
+        a.in_th = g->y_th[cur]; a.in_ph = g->y_ph[cur];
+        a.out_th = nullptr; a.out_ph = g->scratch64;
+        a.t_rhs = t;
+        e = launch_stage_f64(g->model, g->rx, 0, a, g->by, g->stream);
+        if (e == cudaSuccess) {
+            k_maxabs_partial<double, 256><<<nb, 256, 0, g->stream>>>(g->scratch64, g->N, parts);
+            count_launch();
+        }
+    }
+    if (e != cudaSuccess) return fail(g, PF_E_CUDA, std::string("max rate: ") + cudaGetErrorString(e));
+    k_max_final<<<1, 32, 0, g->stream>>>(parts, nb, res);
+    count_launch();
+    PF_CUDA(g, cudaGetLastError());
+    PF_CUDA(g, cudaMemcpyAsync(max_rate, res, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    PF_CUDA(g, cudaStreamSynchronize(g->stream));
+    return PF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,48 @@
+// Instantiations and launcher of the stage kernels, field type float.
+#include "pf_stage.cuh"
+
+namespace pfgb {
+
+namespace {
+using T = float;
+
+template <int MODEL, int RX, int BY>
+cudaError_t launch_by(int stage, const StageArgs<T>& a, cudaStream_t s) {
+    const int n1 = a.cf.n1, n2 = a.cf.n2, n3 = a.cf.n3;
+    dim3 block(TX, BY);
+    dim3 grid((n1 + TX - 1) / TX, (n2 + BY - 1) / BY, (n3 + a.zc - 1) / a.zc);
+    switch (stage) {
+        case 0: stage_kernel<MODEL, RX, T, T, 0, BY><<<grid, block, 0, s>>>(a); break;
+        case 1: stage_kernel<MODEL, RX, T, double, 1, BY><<<grid, block, 0, s>>>(a); break;
+        case 2: stage_kernel<MODEL, RX, T, T, 2, BY><<<grid, block, 0, s>>>(a); break;
+        case 3: stage_kernel<MODEL, RX, T, T, 3, BY><<<grid, block, 0, s>>>(a); break;
+        case 4: stage_kernel<MODEL, RX, T, T, 4, BY><<<grid, block, 0, s>>>(a); break;
+        case 5: stage_kernel<MODEL, RX, T, T, 5, BY><<<grid, block, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int MODEL, int RX>
+cudaError_t launch_m(int stage, const StageArgs<T>& a, int by, cudaStream_t s) {
+    switch (by) {
+        case 4: return launch_by<MODEL, RX, 4>(stage, a, s);
+        case 8: return launch_by<MODEL, RX, 8>(stage, a, s);
+        case 16: return launch_by<MODEL, RX, 16>(stage, a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+}  // namespace
+
+cudaError_t launch_stage_f32(int model, int rx, int stage, const StageArgs<T>& a, int by, cudaStream_t s) {
+    if (a.zc <= 0) return cudaErrorInvalidValue;
+    if (model == M_FULL) return rx == R_GRADP ? launch_m<M_FULL, R_GRADP>(stage, a, by, s)
+                                              : launch_m<M_FULL, R_SIGMA>(stage, a, by, s);
+    if (model == M_TEMP) return launch_m<M_TEMP, R_SIGMA>(stage, a, by, s);
+    if (model == M_MICRO) return rx == R_GRADP ? launch_m<M_MICRO, R_GRADP>(stage, a, by, s)
+                                               : launch_m<M_MICRO, R_SIGMA>(stage, a, by, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace pfgb
