@@ -166,6 +166,30 @@ pf_status pf_max_phase_rate(pf_grid* g, double* max_rate);
  * advances by n_attempts steps.  Synchronises. */
 pf_status pf_profile_stages(pf_grid* g, int n_attempts, double* stage_ms);
 
+/* Unfrozen-water counts that allocate nothing (no counterpart in the paper; a service for callers).
+ *
+ * Some callers cannot call cudaMalloc: a plug-in inside a host application that owns all device
+ * memory through its own pool, a control loop that cannot afford the implicit synchronisation of an
+ * allocation, or a process with a fixed GPU memory budget.  This entry point computes what
+ * pf_unfrozen_fraction computes, on caller-owned device arrays, without creating a grid:
+ *   G, phi : DEVICE arrays of n1*n2*n3 binary64 values (x fastest), borrowed for the call;
+ *   region : host array {i0, i1, j0, j1, k0, k1} (half-open box) or NULL for the whole grid;
+ *   stream : cudaStream_t to enqueue on (NULL = legacy default stream); the call synchronises it;
+ *   outputs: host pointers, any may be NULL (same meaning as in pf_unfrozen_fraction).
+ * Scratch: a file-scope __device__ array of PF_NOALLOC_MAX_PARTIALS + 1 slots of 32 bytes (about
+ * 512 KiB) that every GPU loading the library holds until the process exits.  Each block of the
+ * reduction covers 16384 cells, so a region may hold at most PF_NOALLOC_MAX_PARTIALS * 16384 =
+ * 2^28 cells; larger regions return PF_E_RANGE before any launch.  Bad pointers, sizes or regions
+ * return PF_E_INVALID; CUDA failures PF_E_CUDA.  No cudaMalloc, cudaFree or allocating library call is
+ * made.  The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All calls share the array
+ * and every slot a call reads is written earlier in the same call; calls that overlap on the GPU
+ * (other streams, other host threads) race on it. */
+#define PF_NOALLOC_MAX_PARTIALS 16384
+pf_status pf_unfrozen_fraction_noalloc(const double* G, const double* phi, int n1, int n2, int n3,
+                                       const int* region, void* stream, double* uwc, long long* n_ice,
+                                       long long* n_water, double* smooth);
+
 /* Message of the last failed call on g (or of the last failed pf_create_grid when g is NULL). */
 const char* pf_last_error(const pf_grid* g);
 

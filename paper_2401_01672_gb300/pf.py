@@ -26,7 +26,8 @@ STATUS_NAMES = {0: "PF_OK", -1: "PF_E_INVALID", -2: "PF_E_CUDA", -3: "PF_E_OOM",
 # Every symbol declared in include/pf.h (checked by the CPU tests).
 EXPORTS = ["pf_create_grid", "pf_destroy_grid", "pf_set_geometry", "pf_set_glass", "pf_get_glass", "pf_set_state",
            "pf_get_state", "pf_rhs", "pf_rkm_step", "pf_run_to", "pf_run_fixed", "pf_unfrozen_fraction",
-           "pf_max_phase_rate", "pf_profile_stages", "pf_last_error", "pf_kernel_launches"]
+           "pf_max_phase_rate", "pf_profile_stages", "pf_unfrozen_fraction_noalloc", "pf_last_error",
+           "pf_kernel_launches"]
 
 
 class PfError(RuntimeError):
@@ -81,6 +82,7 @@ def load_library(path: str = LIB_PATH):
         "pf_unfrozen_fraction": [vp, vp, pd, pll, pll, pd],
         "pf_max_phase_rate": [vp, pd],
         "pf_profile_stages": [vp, i, pd],
+        "pf_unfrozen_fraction_noalloc": [vp, vp, i, i, i, vp, vp, pd, pll, pll, pd],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -312,6 +314,23 @@ def pf_max_phase_rate(g):
 
 def pf_profile_stages(g, n_attempts):
     return g.profile_stages(n_attempts)
+
+
+def pf_unfrozen_fraction_noalloc(G_dev, phi_dev, shape, region=None, stream=None):
+    """Unfrozen-water counts on caller-owned device arrays, without any device allocation.
+
+    For callers that cannot allocate GPU memory (the library's reduction scratch is a fixed
+    module global).  Returns (status, dict); status is returned, not raised, so callers can
+    tell PF_E_RANGE (region above the fixed scratch's limit) from other errors.
+    """
+    lib = load_library()
+    r = None if region is None else (C.c_int * 6)(*[int(v) for v in region])
+    u, sm = C.c_double(), C.c_double()
+    ni, nw = C.c_longlong(), C.c_longlong()
+    st = lib.pf_unfrozen_fraction_noalloc(_dev(G_dev), _dev(phi_dev), int(shape[0]), int(shape[1]), int(shape[2]),
+                                          r, None if stream is None else C.c_void_p(stream), C.byref(u),
+                                          C.byref(ni), C.byref(nw), C.byref(sm))
+    return st, {"uwc": u.value, "n_ice": ni.value, "n_water": nw.value, "smooth": sm.value}
 
 
 def pf_kernel_launches():
