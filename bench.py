@@ -43,14 +43,16 @@ SEED = 20240105
 N_SIDE = 256
 TOL = 1e-6
 
-# Algorithmic work per cell and Merson stage of the full SigmaP1-P model (binary64).
-# Bytes: the fused per-stage schedule reads/writes 24 field words per field per step plus
-# the glass field once per stage: (2*24 + 5) * 8 B / 5 stages = 84.8 B.
-BYTES_PER_CELL_STAGE_F64 = (2 * 24 + 5) * 8 / 5
-# Binary32-field form: stage buffers 4 B, state 8 B (see the design doc for the per-stage table).
-BYTES_PER_CELL_STAGE_F32 = (2 * 100 + 5 * 4) / 5
-# Floating-point operations per cell-stage of the method as written.
-FLOPS_PER_CELL_STAGE = 96
+# Algorithmic work per cell of each Merson stage kernel (full SigmaP1-P model); see the design doc.
+# Bytes: stencil input fields + glass field + stage-combination operands read, outputs written,
+# each once per cell.  Binary64 path, bytes per cell for stages 1..5:
+BYTES_F64 = [56, 72, 88, 104, 104]          # sum 424 = 84.8 B per cell-stage
+# Binary32-field form (stage buffers and G in 4 B, state y in 8 B):
+BYTES_F32 = [36, 28, 44, 44, 68]            # sum 220 = 44 B per cell-stage
+# Floating-point operations per cell (FMA = 2, division = 1) of the right-hand side as written
+# (blends 6+6+6, fluxes 24, Allen-Cahn 16, latent coupling 6) plus each stage's combination.
+FLOPS_RHS = 64
+FLOPS_COMB = [4, 6, 8, 12, 24]
 
 
 def env_int(k, d):
@@ -117,65 +119,83 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def make_workload():
-    return I.full_bead_case(N_SIDE, SEED, name="full_sigmap1p_256")
+def make_workload(n=N_SIDE):
+    return I.full_bead_case(n, SEED, name=f"full_sigmap1p_{n}")
+
+
+class OracleCrop:
+    """The oracle as it stands on a 128 x 128 x 32 crop at the top of the workload (Dirichlet face,
+    ice seed, beads), single thread.  Setup (the crop's glass field) is not timed."""
+
+    SHAPE = (128, 128, 32)
+
+    def __init__(self, w):
+        import oracle
+        oracle.build()
+        n = w.shape[0]
+        c = self.SHAPE
+        off = ((n - c[0]) // 2, (n - c[1]) // 2, n - c[2])
+        h = w.h
+        lo = np.array(off) * h
+        hi = (np.array(off) + np.array(c)) * h
+        sp = w.spheres
+        # spheres whose terms can reach the crop (beyond r + 40 xi_G they are below 1e-17)
+        reach = sp[:, 3] + 40 * w.params["xi_G"]
+        near = np.all((sp[:, :3] > lo - reach[:, None]) & (sp[:, :3] < hi + reach[:, None]), axis=1)
+        sps = sp[near].copy()
+        sps[:, :3] -= lo
+        self.o = oracle.Oracle(c, h, w.model, w.reaction, w.params)
+        self.G = self.o.glass(sps, w.params["xi_G"])
+        self.th = np.full(self.o.N, 1.0)
+        self.ph = I.top_slab_indicator(c, 2)
+        self.n_beads = len(sps)
+        self.cells = c[0] * c[1] * c[2]
+
+    def step(self):
+        self.o.rkm_step(self.G, self.th, self.ph, 0.0, 0.01)
+
+    def describe(self, n, el):
+        c = self.SHAPE
+        return (f"{n} Merson steps on a {c[0]}x{c[1]}x{c[2]} crop (top of the {N_SIDE}^3 workload, "
+                f"{self.n_beads} nearby beads), single thread, {el:.1f} s")
 
 
 def cpu_sample(w, seconds=10.0, min_steps=2):
-    """Time the oracle as it stands on a crop of the same workload (single thread)."""
-    import oracle
-    oracle.build()
-    c = (128, 128, 32)
-    off = (64, 64, N_SIDE - c[2])  # top of the vessel: Dirichlet face and ice seed
-    h = w.h
-    lo = np.array(off) * h
-    hi = (np.array(off) + np.array(c)) * h
-    sp = w.spheres
-    # spheres whose terms can reach the crop (beyond r + 40 xi_G they are below 1e-17)
-    reach = sp[:, 3] + 40 * w.params["xi_G"]
-    near = np.all((sp[:, :3] > lo - reach[:, None]) & (sp[:, :3] < hi + reach[:, None]), axis=1)
-    sps = sp[near].copy()
-    sps[:, :3] -= lo
-    o = oracle.Oracle(c, h, w.model, w.reaction, w.params)
-    G = o.glass(sps, w.params["xi_G"])
-    th = np.full(o.N, 1.0)
-    ph = I.top_slab_indicator(c, 2)
+    """cpu_baseline: the oracle timed for about `seconds` on the crop."""
+    oc = OracleCrop(w)
     n, t0 = 0, time.perf_counter()
-    t, dt = 0.0, 0.01
     while True:
-        th1, ph1, E = o.rkm_step(G, th, ph, t, dt)
+        oc.step()
         n += 1
         el = time.perf_counter() - t0
         if n >= min_steps and el >= seconds:
             break
-    cells = c[0] * c[1] * c[2]
-    return {"value": cells * 5 * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} Merson steps on a {c[0]}x{c[1]}x{c[2]} crop (top of the 256^3 workload, "
-                      f"{len(sps)} nearby beads), single thread, {el:.1f} s"}
+    return {"value": oc.cells * 5 * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": oc.describe(n, el)}
 
 
 def run_reference(args, rank, world):
-    """--impl reference: the oracle timed on the host cores (rank 0 only)."""
+    """--impl reference: the oracle timed on the host cores (rank 0 only); one step = one
+    oracle Merson step on the crop."""
     if rank != 0:
         return
     w = make_workload()
-    per = []
+    oc = OracleCrop(w)
     for _ in range(args.warmup):
-        cpu_sample(w, seconds=0.0, min_steps=1)
+        oc.step()
     t0 = time.perf_counter()
-    res = None
     for _ in range(args.steps):
-        res = cpu_sample(w, seconds=0.0, min_steps=1)
-        per.append(res["value"])
+        oc.step()
     el = time.perf_counter() - t0
-    value = statistics.mean(per)
+    value = oc.cells * 5 * args.steps / el
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w.name, "grid": [N_SIDE] * 3, "sample": "128x128x32 crop",
-                                            "l2": "inputs larger than L2 not applicable (CPU)"},
+            "data": "synthetic", "config": {"workload": w.name, "grid": list(w.shape),
+                                            "sample": "128x128x32 crop of the workload",
+                                            "l2": "not applicable (CPU)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": res["sample"]},
+                             "sample": oc.describe(args.steps, el)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -209,6 +229,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-form", action="store_true")
+    ap.add_argument("--size", type=int, default=N_SIDE, help="grid side (256 = the benchmark workload; "
+                    "smaller sizes are for profiling captures only)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -232,7 +254,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    w = make_workload()
+    w = make_workload(args.size)
     stream = torch.cuda.Stream()
     peaks, peak_kind = load_peaks()
 
@@ -277,14 +299,15 @@ def main():
     stage_names = ["stage1", "stage2", "stage3", "stage4", "stage5", "controller"]
     top = int(np.argmax(prof[:5]))
     top_ms = prof[top]
-    flops = FLOPS_PER_CELL_STAGE * w.n_cells
+    flops = (FLOPS_RHS + FLOPS_COMB[top]) * w.n_cells
     fp64_peak_tflops = 152 * 2 * 2 * 2.07e9 / 1e12   # 2 FP64 FMA / clk / SM
     achieved_tf = flops / (top_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": f"merson_{stage_names[top]}_full_sigmap1p_f64",
                 "achieved": achieved_tf, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved_tf / fp64_peak_tflops, "traffic": None,
+                "algorithmic_per_launch": {"flops": flops, "bytes": BYTES_F64[top] * w.n_cells},
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (binary64 pipe)",
-                "hbm_achieved_gbs": BYTES_PER_CELL_STAGE_F64 * w.n_cells / (top_ms * 1e-3) / 1e9,
+                "hbm_achieved_gbs": BYTES_F64[top] * w.n_cells / (top_ms * 1e-3) / 1e9,
                 "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peak_kind,
                 "stage_ms": dict(zip(stage_names, prof))}
 
@@ -314,13 +337,14 @@ def main():
         g32, s32, ms32, l32, prof32 = time_form(torch, pf, w, I.PREC_FP32, args.steps, args.warmup, stream)
         att32 = s32["n_accepted"] + s32["n_rejected"]
         top32 = int(np.argmax(prof32[:5]))
+        gbs32 = BYTES_F32[top32] * w.n_cells / (prof32[top32] * 1e-3) / 1e9
         forms["fp32_fields"] = {
             "value": w.n_cells * 5 * att32 / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32 / max(att32, 1),
             "gpu_launches": l32, "dtype": "f32 fields / f64 state",
             "roofline": {"bound": "hbm", "kernel": f"merson_{stage_names[top32]}_full_sigmap1p_f32",
-                         "achieved": BYTES_PER_CELL_STAGE_F32 * w.n_cells / (prof32[top32] * 1e-3) / 1e9,
-                         "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": BYTES_PER_CELL_STAGE_F32 * w.n_cells / (prof32[top32] * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                         "achieved": gbs32, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": gbs32 / peaks["hbm_gbs"],
+                         "step_gbs": sum(BYTES_F32) * w.n_cells / (sum(prof32[:5]) * 1e-3) / 1e9,
                          "traffic": None, "peak_source": peak_kind,
                          "stage_ms": dict(zip(stage_names, prof32))}}
         g32.close()

@@ -27,6 +27,8 @@ struct pf_grid {
     int model = 0, rx = 0, prec = 0;
     pf_params p{};
     Coefs cf{};
+    CoefT<double> k64{};
+    CoefT<float> k32{};
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
     int by = 8, zc = 32;
@@ -197,6 +199,7 @@ __global__ void k_controller(Ctrl* c) {
         c->dt_step = c->dt;
         c->land = 0;
     }
+    prepare_step(c);
 }
 
 // UWC partial sums over a half-open box; one slot of 4 words per block:
@@ -249,17 +252,29 @@ __global__ void __launch_bounds__(BS) k_uwc_partial(const double* __restrict__ G
     if (threadIdx.x == 0) parts[blockIdx.x] = sp[0];
 }
 
-// Fixed-order final sum of the per-block partials (deterministic binary64 result).
-__global__ void k_uwc_final(UwcPart* parts, int nparts, UwcPart* out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Fixed-order final sum of the per-block partials (deterministic binary64 result): thread t sums
+// partials t, t+256, ... in order, then a fixed tree combines the 256 thread sums.
+__global__ void __launch_bounds__(256) k_uwc_final(UwcPart* parts, int nparts, UwcPart* out) {
+    __shared__ UwcPart s[256];
     UwcPart acc = {0, 0, 0.0, 0.0};
-    for (int b = 0; b < nparts; ++b) {
+    for (int b = threadIdx.x; b < nparts; b += 256) {
         acc.nw += parts[b].nw;
         acc.ni += parts[b].ni;
         acc.sn += parts[b].sn;
         acc.sd += parts[b].sd;
     }
-    *out = acc;
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            s[threadIdx.x].nw += s[threadIdx.x + h].nw;
+            s[threadIdx.x].ni += s[threadIdx.x + h].ni;
+            s[threadIdx.x].sn += s[threadIdx.x + h].sn;
+            s[threadIdx.x].sd += s[threadIdx.x + h].sd;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0];
 }
 
 // max |v| over n values of type T -> per-block partial maxima (binary64), then a final pass.
@@ -288,11 +303,35 @@ __global__ void k_max_final(const double* parts, int n, double* out) {
     *out = m;
 }
 
+// Model constants in the stage kernels' form, computed in binary64 (see CoefT).
+template <typename T>
+static void fill_coefs(CoefT<T>& k, const pf_params& p, double h) {
+    const double s = 0.5 / (h * h);
+    k.lamL = T(p.lambda[0] * s);
+    k.dLG = T((p.lambda[2] - p.lambda[0]) * s);
+    k.dLI = T((p.lambda[1] - p.lambda[0]) * s);
+    k.rhoL = T(p.rho[0]); k.dRG = T(p.rho[2] - p.rho[0]); k.dRI = T(p.rho[1] - p.rho[0]);
+    k.capL = T(p.c[0]); k.dCG = T(p.c[2] - p.c[0]); k.dCI = T(p.c[1] - p.c[0]);
+    k.latent = T(p.latent);
+    const double w = (p.alpha > 0 && p.xi > 0) ? 2.0 / (p.alpha * p.xi * p.xi) : 0.0;
+    k.wa = T(w);
+    k.wb = T(-p.zeta * w);
+    k.klap = T(p.xi * p.xi * s);
+    k.ksig = T(0.5 * p.xi * p.b * p.mu * p.alpha);
+    k.kgrad = T(p.xi * p.xi * p.mu * p.alpha / (4.0 * h));
+    k.eps0 = T(p.eps0); k.eps1 = T(p.eps1);
+    k.inv_de = T(p.eps1 > p.eps0 ? 1.0 / (p.eps1 - p.eps0) : 0.0);
+    k.gamma = T(p.gamma); k.zeta = T(p.zeta);
+    k.theta_micro = T(p.theta_micro);
+}
+
 // ------------------------------------------------------------------ stage dispatch
 template <typename T>
 static StageArgs<T> make_args(pf_grid* g) {
     StageArgs<T> a{};
     a.cf = g->cf;
+    if constexpr (std::is_same<T, float>::value) a.k = g->k32;
+    else a.k = g->k64;
     a.ctrl = g->dctrl;
     for (int b = 0; b < 2; ++b) {
         a.y_th[b] = g->y_th[b];
@@ -424,20 +463,9 @@ pf_status pf_create_grid(int n1, int n2, int n3, double h, int model, int reacti
     c.n1 = n1; c.n2 = n2; c.n3 = n3;
     c.dirichlet = (model == PF_MODEL_MICRO) ? 0 : (p->dirichlet_faces & 63);
     c.harmonic = p->harmonic_mean ? 1 : 0;
-    c.inv_h2 = 1.0 / (h * h);
-    c.half_inv_h2 = 0.5 / (h * h);
-    for (int m = 0; m < 3; ++m) { c.lam[m] = p->lambda[m]; c.rho[m] = p->rho[m]; c.cap[m] = p->c[m]; }
-    c.latent = p->latent;
-    c.xi2 = p->xi * p->xi;
-    c.inv_axi2 = (p->alpha > 0 && p->xi > 0) ? 1.0 / (p->alpha * p->xi * p->xi) : 0.0;
-    c.ksig = 0.5 * p->xi * p->b * p->mu * p->alpha;
-    c.kgrad = p->xi * p->xi * p->mu * p->alpha / (2.0 * h);
-    c.eps0 = p->eps0; c.eps1 = p->eps1;
-    c.inv_de = (p->eps1 > p->eps0) ? 1.0 / (p->eps1 - p->eps0) : 0.0;
-    c.gamma = p->gamma; c.zeta = p->zeta;
-    c.theta_micro = p->theta_micro;
     c.theta_freeze = p->theta_freeze; c.theta_thaw = p->theta_thaw; c.t_freeze = p->t_freeze;
-
+    fill_coefs(g->k64, *p, h);
+    fill_coefs(g->k32, *p, h);
     auto alloc = [&](size_t bytes) -> void* {
         void* q = nullptr;
         if (cudaMalloc(&q, bytes) != cudaSuccess) return nullptr;
@@ -494,6 +522,8 @@ pf_status pf_create_grid(int n1, int n2, int n3, double h, int model, int reacti
     std::memset(g->hctrl, 0, sizeof(Ctrl));
     g->hctrl->dt = std::isfinite(p->dt_max) ? p->dt_max : 1e-3;
     g->hctrl->t_freeze = p->t_freeze;
+    g->hctrl->theta_freeze = p->theta_freeze;
+    g->hctrl->theta_thaw = p->theta_thaw;
     g->hctrl->dt_min = p->dt_min;
     g->hctrl->dt_max = p->dt_max;
     if (push_ctrl(g) != PF_OK || cudaStreamSynchronize(g->stream) != cudaSuccess) {
@@ -658,6 +688,7 @@ pf_status pf_rkm_step(pf_grid* g, double* dt_inout, double tol, int force_accept
     c->dt_step = *dt_inout;
     c->dt = *dt_inout;
     c->land = 0;
+    prepare_step(c);
     c->done = 0;
     c->status = 0;
     c->fixed = force_accept ? 1 : 0;
@@ -678,7 +709,8 @@ pf_status pf_rkm_step(pf_grid* g, double* dt_inout, double tol, int force_accept
 }
 
 static pf_status run_loop(pf_grid* g, pf_run_stats* stats) {
-    const int steps_per_graph = 16;
+    const long long want = g->hctrl->max_attempts;
+    const int steps_per_graph = want >= 16 ? 16 : (want >= 4 ? 4 : 1);
     if (!g->graph || g->graph_steps != steps_per_graph) {
         pf_status s = build_graph(g, steps_per_graph);
         if (s != PF_OK) return s;
@@ -720,6 +752,7 @@ static void first_step(Ctrl* c) {
         c->dt_step = c->dt;
         c->land = 0;
     }
+    prepare_step(c);
 }
 
 pf_status pf_run_to(pf_grid* g, double t_end, double tol, long long max_steps, pf_run_stats* stats) {
@@ -787,7 +820,7 @@ pf_status pf_unfrozen_fraction(pf_grid* g, const int* region, double* uwc, long 
     k_uwc_partial<256><<<nb, 256, 0, g->stream>>>(g->G64, (const double* const*)tab, (const double* const*)(tab + 2),
                                                   g->dctrl, g->model == PF_MODEL_TEMP, g->p.gamma, g->p.zeta, g->n1,
                                                   g->n2, r[0], r[1], r[2], r[3], r[4], r[5], parts);
-    k_uwc_final<<<1, 32, 0, g->stream>>>(parts, nb, res);
+    k_uwc_final<<<1, 256, 0, g->stream>>>(parts, nb, res);
     count_launch(2);
     g->launches += 2;
     PF_CUDA(g, cudaGetLastError());
@@ -811,6 +844,7 @@ pf_status pf_profile_stages(pf_grid* g, int n_attempts, double* stage_ms) {
     c->single = 1;
     c->dt_step = c->dt;
     c->land = 0;
+    prepare_step(c);
     c->done = 0;
     c->status = 0;
     c->err_bits = 0;

@@ -12,24 +12,38 @@ enum { R_SIGMA = 0, R_GRADP = 1 };
 // each thread marches along z over a chunk of ZC planes.
 constexpr int TX = 32;
 
-// Model constants, precomputed on the host in binary64 (Secs. 2.1-2.5).
+// Model constants in the form the stage kernels use them, filled on the host
+// (binary64 arithmetic) for each field type, so kernels convert nothing.
+//   lambda = lamL + G dLG + (1 - G) phi dLI, scaled by 1/(2 h^2)  (eq. material-properties-blending-formula)
+//   rho, c : same blend, unscaled
+//   2 I_W/(alpha xi^2) = max(0, wa + wb G)                         (eqs. water-indicator, Allen-Cahn-equation)
+template <typename T>
+struct CoefT {
+    T lamL, dLG, dLI;
+    T rhoL, dRG, dRI;
+    T capL, dCG, dCI;
+    T latent;
+    T wa, wb;
+    T klap;      // xi^2 / (2 h^2)
+    T ksig;      // xi b mu alpha / 2                (SigmaP1-P)
+    T kgrad;     // xi^2 mu alpha / (4 h)            (GradP, central differences)
+    T eps0, eps1, inv_de;
+    T gamma, zeta;
+    T theta_micro;
+};
+
+// Grid-wide integer constants.
 struct Coefs {
     int n1, n2, n3;
     int dirichlet;      // PF_FACE_* bits
     int harmonic;       // face conductivity: harmonic mean
     int pad0;
-    double inv_h2;      // 1/h^2
-    double half_inv_h2; // 1/(2 h^2): arithmetic-mean face conductivity folded in
-    double lam[3], rho[3], cap[3]; // liquid, ice, glass
-    double latent;
-    double xi2;         // xi^2
-    double inv_axi2;    // 1/(alpha xi^2)
-    double ksig;        // 1/2 xi b mu alpha      (SigmaP1-P)
-    double kgrad;       // xi^2 mu alpha / (2h)   (GradP, central differences)
-    double eps0, eps1, inv_de;
-    double gamma, zeta;
-    double theta_micro, theta_freeze, theta_thaw, t_freeze;
+    double theta_freeze, theta_thaw, t_freeze;
 };
+
+// Merson stage coefficients of the step being taken (dt = dt_step):
+// [0] dt/3 [1] dt/6 [2] dt/8 [3] 3dt/8 [4] dt/2 [5] 3dt/2 [6] 2dt [7] dt/30 [8] 5dt/24 [9] 15dt/8
+constexpr int NSC = 10;
 
 // Device-resident step control (one per grid).  All per-step scalars live
 // here so that a captured CUDA graph can be replayed without host updates.
@@ -39,7 +53,13 @@ struct Ctrl {
     double dt_step;    // size of the step being taken (shortened to land on target)
     double target;     // landing time when land != 0
     double tol, t_end, t_freeze, dt_min, dt_max;
+    double theta_freeze, theta_thaw;
     double last_err;
+    double theta_b;    // Dirichlet value of the step being taken
+    double sc[NSC];    // stage coefficients, binary64
+    float scf[NSC];    // stage coefficients, binary32
+    float theta_bf;
+    int pad1;
     unsigned long long err_bits;  // max of the error estimate over cells (bit pattern of a double >= 0)
     long long n_acc, n_rej, max_attempts;
     int cur;           // state buffer holding y
@@ -52,9 +72,24 @@ struct Ctrl {
     int pad;
 };
 
+// Stage coefficients and the boundary value for the step (t, dt_step): the
+// Dirichlet value of the interval the step lies in (t < t_freeze -> freeze value).
+__host__ __device__ inline void prepare_step(Ctrl* c) {
+    const double dt = c->dt_step;
+    const double v[NSC] = {dt / 3.0, dt / 6.0, dt / 8.0, 3.0 * dt / 8.0, dt / 2.0,
+                           1.5 * dt, 2.0 * dt, dt / 30.0, 5.0 * dt / 24.0, 15.0 * dt / 8.0};
+    for (int q = 0; q < NSC; ++q) {
+        c->sc[q] = v[q];
+        c->scf[q] = (float)v[q];
+    }
+    c->theta_b = (c->t < c->t_freeze) ? c->theta_freeze : c->theta_thaw;
+    c->theta_bf = (float)c->theta_b;
+}
+
 template <typename T>
 struct StageArgs {
     Coefs cf;
+    CoefT<T> k;
     Ctrl* ctrl;
     const double* y_th[2];   // state double buffer (binary64 in both precisions)
     const double* y_ph[2];

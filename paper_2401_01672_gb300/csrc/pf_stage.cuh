@@ -10,20 +10,28 @@
 //   stage 5: k5 = F(u5), y' = y + dt/6 (k1 + 4k4 + k5), E = max |dt/30 (2k1 - 9k3 + 8k4 - k5)|
 // k2 and k5 are never stored.  Stage 0 is the plain right-hand side.
 //
-// Tiling: a block of 32 x BY threads owns a 32 x BY column of cells and
-// marches along z over ZC planes.  Plane k (with a one-cell lateral halo)
-// sits in shared memory together with the blended conductivity of every
-// cell, so each cell's lambda is evaluated once per plane visit; the z
-// neighbours of a thread's own column stay in registers.  Cells outside
-// the grid are replaced by the nearest boundary cell (mirror ghost), which
-// makes the interior formula give zero flux on every face; Dirichlet faces
-// add their half-cell flux separately.
+// Tiling: a block of 32 x BY threads owns a 32 x BY column of cells and marches
+// along z over ZC planes.  Plane k (with a one-cell lateral halo) sits in shared
+// memory together with the blended conductivity of every cell, so each cell's
+// lambda is evaluated once per plane visit; the z neighbours of a thread's own
+// column stay in registers.  The raw values of plane k+2 are loaded while plane
+// k is computed (three-plane shared-memory ring, one barrier per plane), and the
+// stage-combination operands are loaded before the right-hand-side arithmetic,
+// so memory latency overlaps computation.  Cells outside the grid are replaced by
+// the nearest boundary cell (mirror ghost), which makes the interior formula give
+// zero flux on every face; Dirichlet faces add their half-cell flux separately.
 //
-// Binary32 form (T = float): stage inputs chain from one stage input to the
-// next (u3 = u2 + dt/6 (k2 - k1), u4 = u2 - 5dt/24 k1 + 3dt/8 k3,
-// u5 = u4 + 3dt/8 k1 - 15dt/8 k3 + 2dt k4 -- algebraically the tableau rows)
-// so that only stages 1 and 5 touch the binary64 state; the state update
-// y' = y + (dt/6 (k1 + 4k4 + k5)) adds a binary32 increment to binary64 y.
+// Binary64 operation count: the binary64 pipe of sm_103a issues two FMAs per clock
+// per SM, a sixtieth of the binary32 rate, so the binary64 kernels keep every
+// comparison, absolute value and maximum in integer instructions on the IEEE bit
+// patterns, take blends as three FMAs, and divide with a Newton-Raphson reciprocal
+// seeded by the binary32 reciprocal.
+//
+// Binary32 form (T = float): stage inputs chain from one stage input to the next
+// (u3 = u2 + dt/6 (k2 - k1), u4 = u2 - 5dt/24 k1 + 3dt/8 k3,
+// u5 = u4 + 3dt/8 k1 - 15dt/8 k3 + 2dt k4 -- algebraically the tableau rows) so that
+// only stages 1 and 5 touch the binary64 state; the state update y' = y + (dt/6 (k1 +
+// 4k4 + k5)) adds a binary32 increment to binary64 y.
 #pragma once
 #include "pf_internal.cuh"
 #include <cfloat>
@@ -35,58 +43,67 @@ __device__ __forceinline__ double dtanh(double x) { return tanh(x); }
 __device__ __forceinline__ float dtanh(float x) { return tanhf(x); }
 __device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double FMA(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float FMA(float a, float b, float c) { return fmaf(a, b, c); }
+
+// Comparisons against a non-negative constant y through the IEEE bit pattern
+// (signed-integer order equals numeric order for x >= -0 and puts negatives first).
+__device__ __forceinline__ bool le_nonneg(double x, double y) { return __double_as_longlong(x) <= __double_as_longlong(y); }
+__device__ __forceinline__ bool le_nonneg(float x, float y) { return x <= y; }
+__device__ __forceinline__ bool ge_nonneg(double x, double y) { return __double_as_longlong(x) >= __double_as_longlong(y); }
+__device__ __forceinline__ bool ge_nonneg(float x, float y) { return x >= y; }
+__device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool positive(float x) { return x > 0.f; }
+
+// 1/x for x > 0: Newton-Raphson iteration r <- r + r (1 - x r), twice, from the binary32
+// reciprocal of x's leading 20 mantissa bits (relative error 2^-20 -> 2^-40 -> below 1 ulp).
+// The binary32 seed is built from the bit pattern with integer instructions.
+__device__ __forceinline__ double recip_pos(double x) {
+    const long long b = __double_as_longlong(x);
+    const int hi = (int)(b >> 32);
+    const int e = ((hi >> 20) & 0x7FF) - 1023 + 127;
+    if (b <= 0 || e < 2 || e > 252) return 1.0 / x;
+    const float xf = __int_as_float((e << 23) | ((hi & 0xFFFFF) << 3));
+    const int bf = __float_as_int(__frcp_rn(xf));
+    const long long er = (long long)(((bf >> 23) & 0xFF) - 127 + 1023);
+    double r = __longlong_as_double((er << 52) | ((long long)(bf & 0x7FFFFF) << 29));
+    double d = fma(-x, r, 1.0);
+    r = fma(r, d, r);
+    d = fma(-x, r, 1.0);
+    r = fma(r, d, r);
+    return r;
+}
+__device__ __forceinline__ float recip_pos(float x) { return __frcp_rn(x); }
 
 // eq. (Sigma-limiter)
 template <typename T>
-__device__ __forceinline__ T sigma_lim(T w, T e0, T e1, T inv_de) {
-    if (w <= e0) return T(0);
-    if (w >= e1) return T(1);
-    T s = (w - e0) * inv_de;
-    return s * s * (T(3) - T(2) * s);
+__device__ __forceinline__ T sigma_lim(T w, const CoefT<T>& k) {
+    if (le_nonneg(w, k.eps0)) return T(0);
+    if (ge_nonneg(w, k.eps1)) return T(1);
+    const T s = (w - k.eps0) * k.inv_de;
+    return s * s * FMA(T(-2), s, T(3));
 }
 
-// eq. (material-properties-blending-formula)
+// eq. (material-properties-blending-formula): w0 + G dG + (1 - G) phi dI
 template <typename T>
-__device__ __forceinline__ T blend(T G, T ph, T wL, T wI, T wG) {
-    return G * wG + (T(1) - G) * (ph * wI + (T(1) - ph) * wL);
+__device__ __forceinline__ T blend3(T G, T ph, T w0, T dG, T dI) {
+    return FMA(ph, FMA(-G, dI, dI), FMA(G, dG, w0));
 }
 
 // eq. (water-indicator)
 template <typename T>
 __device__ __forceinline__ T water_ind(T G, T zeta) {
-    T v = T(1) - zeta * G;
-    return v > T(0) ? v : T(0);
+    const T v = FMA(-zeta, G, T(1));
+    return positive(v) ? v : T(0);
 }
 
 template <typename T>
-struct CoefT {
-    T inv_h2, half_inv_h2;
-    T lamL, lamI, lamG, rhoL, rhoI, rhoG, cL, cI, cG;
-    T latent, xi2, inv_axi2, ksig, kgrad, eps0, eps1, inv_de, gamma, zeta;
-    T theta_micro;
-    __device__ __forceinline__ explicit CoefT(const Coefs& c)
-        : inv_h2(T(c.inv_h2)), half_inv_h2(T(c.half_inv_h2)),
-          lamL(T(c.lam[0])), lamI(T(c.lam[1])), lamG(T(c.lam[2])),
-          rhoL(T(c.rho[0])), rhoI(T(c.rho[1])), rhoG(T(c.rho[2])),
-          cL(T(c.cap[0])), cI(T(c.cap[1])), cG(T(c.cap[2])),
-          latent(T(c.latent)), xi2(T(c.xi2)), inv_axi2(T(c.inv_axi2)), ksig(T(c.ksig)),
-          kgrad(T(c.kgrad)), eps0(T(c.eps0)), eps1(T(c.eps1)), inv_de(T(c.inv_de)),
-          gamma(T(c.gamma)), zeta(T(c.zeta)), theta_micro(T(c.theta_micro)) {}
-};
-
-// Load one cell of the stage input: theta, phi (the Temp model's phi(theta),
-// eq. explicit-p-dependence-on-T), blended conductivity and G.
-template <int MODEL, typename T, typename TIN>
-__device__ __forceinline__ void load_cell(const CoefT<T>& c, const TIN* __restrict__ in_th,
-                                          const TIN* __restrict__ in_ph, const T* __restrict__ Gf,
-                                          long long id, T& th, T& ph, T& lam, T& G) {
-    G = Gf[id];
-    if constexpr (MODEL == M_MICRO) th = c.theta_micro;
-    else th = T(in_th[id]);
-    if constexpr (MODEL == M_TEMP) ph = T(0.5) * water_ind(G, c.zeta) * (T(1) - dtanh(c.gamma * th));
-    else ph = T(in_ph[id]);
-    if constexpr (MODEL == M_MICRO) lam = T(0);
-    else lam = blend(G, ph, c.lamL, c.lamI, c.lamG);
+__device__ __forceinline__ unsigned long long abs_bits(T v) {
+    if constexpr (std::is_same<T, double>::value) {
+        return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFULL;
+    } else {
+        return (unsigned long long)((unsigned)__float_as_int(v) & 0x7FFFFFFFu);
+    }
 }
 
 template <int MODEL, int RX, typename T, typename TIN, int STAGE, int BY>
@@ -97,28 +114,55 @@ stage_kernel(const StageArgs<T> a) {
     constexpr bool HAS_TH = (MODEL != M_MICRO);  // theta integrated
     constexpr bool HAS_PH = (MODEL != M_TEMP);   // phi integrated
     constexpr bool F32 = std::is_same<T, float>::value;
+    constexpr bool TEMP = (MODEL == M_TEMP);
 
     Ctrl* ctrl = a.ctrl;
     int cur = 0;
-    double dt = 0.0, tstart = a.t_rhs;
+    T th_b;
+    T sc[NSC];
     if constexpr (STAGE != 0) {
         if (ctrl->done) return;  // uniform across the grid
         cur = ctrl->cur;
-        dt = ctrl->dt_step;
-        tstart = ctrl->t;
+        if constexpr (F32) {
+            th_b = ctrl->theta_bf;
+#pragma unroll
+            for (int q = 0; q < NSC; ++q) sc[q] = ctrl->scf[q];
+        } else {
+            th_b = ctrl->theta_b;
+#pragma unroll
+            for (int q = 0; q < NSC; ++q) sc[q] = ctrl->sc[q];
+        }
+    } else {
+        th_b = T((a.t_rhs < a.cf.t_freeze) ? a.cf.theta_freeze : a.cf.theta_thaw);
+#pragma unroll
+        for (int q = 0; q < NSC; ++q) sc[q] = T(0);
     }
-    const Coefs& cf = a.cf;
-    const CoefT<T> c(cf);
-    const int n1 = cf.n1, n2 = cf.n2, n3 = cf.n3;
+    const CoefT<T>& K = a.k;
+    const int n1 = a.cf.n1, n2 = a.cf.n2, n3 = a.cf.n3;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i = blockIdx.x * TX + tx, j = blockIdx.y * BY + ty;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * BY;
+    const int i = i0 + tx, j = j0 + ty;
     const int kb = blockIdx.z * a.zc;
     const int ke = min(kb + a.zc, n3);
-    const int ic = min(i, n1 - 1), jc = min(j, n2 - 1);
     const bool inside = (i < n1) && (j < n2);
     const long long plane = (long long)n1 * n2;
-    const int ixm = min(max(i - 1, 0), n1 - 1), ixp = min(i + 1, n1 - 1);
-    const int jym = min(max(j - 1, 0), n2 - 1), jyp = min(j + 1, n2 - 1);
+    const long long ooff = (long long)min(j, n2 - 1) * n1 + min(i, n1 - 1);
+
+    // one halo cell per thread for the first 2 TX + 2 BY threads: y rows, then x columns
+    const int tid = ty * TX + tx;
+    bool hal = false;
+    int hx = 0, hy = 0;
+    if (tid < 2 * TX) {
+        hal = true;
+        hx = tid % TX;
+        hy = (tid < TX) ? -1 : BY;
+    } else if (tid < 2 * TX + 2 * BY) {
+        hal = true;
+        const int r = tid - 2 * TX;
+        hy = r % BY;
+        hx = (r < BY) ? -1 : TX;
+    }
+    const long long hoff = (long long)min(max(j0 + hy, 0), n2 - 1) * n1 + min(max(i0 + hx, 0), n1 - 1);
 
     const TIN* in_th = nullptr;
     const TIN* in_ph = nullptr;
@@ -135,128 +179,182 @@ stage_kernel(const StageArgs<T> a) {
         in_th = reinterpret_cast<const TIN*>(a.ub_th);
         in_ph = reinterpret_cast<const TIN*>(a.ub_ph);
     }
+    const T* __restrict__ Gf = a.G;
 
     constexpr int SX = TX + 2, SY = BY + 2;
-    __shared__ T s_th[2][SY][SX];
-    __shared__ T s_ph[2][SY][SX];
-    __shared__ T s_lam[2][SY][SX];
+    __shared__ T s_th[HAS_TH ? 3 : 1][SY][SX];
+    __shared__ T s_ph[3][SY][SX];
+    __shared__ T s_lam[HAS_TH ? 3 : 1][SY][SX];
 
-    const T* __restrict__ Gf = a.G;
-    auto load_plane = [&](int kk, int b, T& th, T& ph, T& lam, T& G) {
-        const int kc = min(max(kk, 0), n3 - 1);
-        const long long base = (long long)kc * plane;
-        load_cell<MODEL, T, TIN>(c, in_th, in_ph, Gf, base + (long long)jc * n1 + ic, th, ph, lam, G);
-        s_th[b][ty + 1][tx + 1] = th;
-        s_ph[b][ty + 1][tx + 1] = ph;
-        s_lam[b][ty + 1][tx + 1] = lam;
-        T h_th, h_ph, h_lam, h_G;
-        if (tx == 0) {
-            load_cell<MODEL, T, TIN>(c, in_th, in_ph, Gf, base + (long long)jc * n1 + ixm, h_th, h_ph, h_lam, h_G);
-            s_th[b][ty + 1][0] = h_th; s_ph[b][ty + 1][0] = h_ph; s_lam[b][ty + 1][0] = h_lam;
+    // raw loads of one cell of plane kk (clamped: mirror ghosts)
+    auto fetch = [&](int kk, long long off, T& th, T& ph, T& G) {
+        const long long id = (long long)min(max(kk, 0), n3 - 1) * plane + off;
+        G = Gf[id];
+        if constexpr (HAS_TH) th = T(in_th[id]);
+        else th = K.theta_micro;
+        if constexpr (HAS_PH) ph = T(in_ph[id]);
+        else ph = T(0);
+    };
+    // derived values: Temp phase field (eq. explicit-p-dependence-on-T) and blended conductivity
+    auto finish = [&](T th, T& ph, T G, T& lam, T& tg) {
+        if constexpr (TEMP) {
+            tg = dtanh(K.gamma * th);
+            ph = T(0.5) * water_ind(G, K.zeta) * (T(1) - tg);
         }
-        if (tx == TX - 1) {
-            load_cell<MODEL, T, TIN>(c, in_th, in_ph, Gf, base + (long long)jc * n1 + ixp, h_th, h_ph, h_lam, h_G);
-            s_th[b][ty + 1][TX + 1] = h_th; s_ph[b][ty + 1][TX + 1] = h_ph; s_lam[b][ty + 1][TX + 1] = h_lam;
+        if constexpr (HAS_TH) lam = blend3(G, ph, K.lamL, K.dLG, K.dLI);
+        else lam = T(0);
+    };
+    auto put = [&](int b, int y, int x, T th, T ph, T lam) {
+        if constexpr (HAS_TH) {
+            s_th[b][y][x] = th;
+            s_lam[b][y][x] = lam;
         }
-        if (ty == 0) {
-            load_cell<MODEL, T, TIN>(c, in_th, in_ph, Gf, base + (long long)jym * n1 + ic, h_th, h_ph, h_lam, h_G);
-            s_th[b][0][tx + 1] = h_th; s_ph[b][0][tx + 1] = h_ph; s_lam[b][0][tx + 1] = h_lam;
-        }
-        if (ty == BY - 1) {
-            load_cell<MODEL, T, TIN>(c, in_th, in_ph, Gf, base + (long long)jyp * n1 + ic, h_th, h_ph, h_lam, h_G);
-            s_th[b][BY + 1][tx + 1] = h_th; s_ph[b][BY + 1][tx + 1] = h_ph; s_lam[b][BY + 1][tx + 1] = h_lam;
-        }
+        s_ph[b][y][x] = ph;
     };
 
     // Dirichlet faces of this column (x and y faces are fixed along the march)
-    const double t_b = (tstart < cf.t_freeze) ? cf.theta_freeze : cf.theta_thaw;
-    const T th_b = T(t_b);
+    const int dmask = a.cf.dirichlet;
     int nd_xy = 0;
-    if (cf.dirichlet) {
-        nd_xy += ((cf.dirichlet & 1) && i == 0) + ((cf.dirichlet & 2) && i == n1 - 1);
-        nd_xy += ((cf.dirichlet & 4) && j == 0) + ((cf.dirichlet & 8) && j == n2 - 1);
+    if (dmask) {
+        nd_xy += ((dmask & 1) && i == 0) + ((dmask & 2) && i == n1 - 1);
+        nd_xy += ((dmask & 4) && j == 0) + ((dmask & 8) && j == n2 - 1);
     }
 
-    // stage coefficients
-    const T c13 = T(dt / 3.0), c16 = T(dt / 6.0), c18 = T(dt / 8.0), c38 = T(3.0 * dt / 8.0);
-    const T c12 = T(dt / 2.0), c32 = T(1.5 * dt), c2 = T(2.0 * dt), c30 = T(dt / 30.0);
-    const T c524 = T(5.0 * dt / 24.0), c158 = T(15.0 * dt / 8.0);
-
-    T thm, phm, lamm, Gm, thc, phc, lamc, Gc, thp, php, lamp, Gp;
+    // ---- prologue: own column at kb-1, kb, kb+1; planes kb, kb+1 into the ring
+    T thm, phm, lamm, tgm = T(0);
+    T thc, phc, lamc, Gc, tgc = T(0);
+    T thp, php, lamp, Gp, tgp = T(0);
     {
-        const int km = min(max(kb - 1, 0), n3 - 1);
-        load_cell<MODEL, T, TIN>(c, in_th, in_ph, Gf, (long long)km * plane + (long long)jc * n1 + ic, thm, phm,
-                                 lamm, Gm);
+        T Gm;
+        fetch(kb - 1, ooff, thm, phm, Gm);
+        finish(thm, phm, Gm, lamm, tgm);
+        fetch(kb, ooff, thc, phc, Gc);
+        finish(thc, phc, Gc, lamc, tgc);
+        put(0, ty + 1, tx + 1, thc, phc, lamc);
+        fetch(kb + 1, ooff, thp, php, Gp);
+        finish(thp, php, Gp, lamp, tgp);
+        put(1, ty + 1, tx + 1, thp, php, lamp);
+        if (hal) {
+            T h_th, h_ph, h_G, h_lam, h_tg;
+            fetch(kb, hoff, h_th, h_ph, h_G);
+            finish(h_th, h_ph, h_G, h_lam, h_tg);
+            put(0, hy + 1, hx + 1, h_th, h_ph, h_lam);
+            fetch(kb + 1, hoff, h_th, h_ph, h_G);
+            finish(h_th, h_ph, h_G, h_lam, h_tg);
+            put(1, hy + 1, hx + 1, h_th, h_ph, h_lam);
+        }
     }
-    load_plane(kb, 0, thc, phc, lamc, Gc);
     __syncthreads();
 
-    T emax = T(0);
-    bool nonfinite = false;
+    unsigned long long ebits = 0ULL;  // max |E| as a bit pattern (NaN/Inf sort above every finite value)
+    int b = 0;
 
     for (int k = kb; k < ke; ++k) {
-        const int b = (k - kb) & 1;
-        load_plane(k + 1, b ^ 1, thp, php, lamp, Gp);
+        // 1. raw values of plane k+2 (consumed after the arithmetic of plane k)
+        T rth, rph, rG, qth, qph, qG;
+        fetch(k + 2, ooff, rth, rph, rG);
+        if (hal) fetch(k + 2, hoff, qth, qph, qG);
+
+        const long long id = (long long)k * plane + (long long)j * n1 + i;
+        // 2. stage-combination operands of this cell
+        T y_t = T(0), y_p = T(0), k1t = T(0), k1p = T(0), k3t = T(0), k3p = T(0), k4t = T(0), k4p = T(0);
+        double y_t64 = 0.0, y_p64 = 0.0;
+        T ua_t = T(0), ua_p = T(0);
         if (inside) {
-            const long long id = (long long)k * plane + (long long)j * n1 + i;
-            // ---- heat flux divergence (eq. heat-equation), per-face conductivity
+            if constexpr (STAGE >= 2) {
+                if constexpr (HAS_TH) k1t = a.k1_th[id];
+                if constexpr (HAS_PH) k1p = a.k1_ph[id];
+            }
+            if constexpr (STAGE >= 4) {
+                if constexpr (HAS_TH) k3t = a.k3_th[id];
+                if constexpr (HAS_PH) k3p = a.k3_ph[id];
+            }
+            if constexpr (STAGE == 5) {
+                if constexpr (HAS_TH) { k4t = a.k4_th[id]; y_t64 = a.y_th[cur][id]; }
+                if constexpr (HAS_PH) { k4p = a.k4_ph[id]; y_p64 = a.y_ph[cur][id]; }
+            }
+            if constexpr (!F32 && STAGE >= 2 && STAGE <= 4) {
+                if constexpr (HAS_TH) y_t = a.y_th[cur][id];
+                if constexpr (HAS_PH) y_p = a.y_ph[cur][id];
+            }
+            if constexpr (F32 && STAGE == 3) {
+                if constexpr (HAS_TH) ua_t = a.ua_th[id];
+                if constexpr (HAS_PH) ua_p = a.ua_ph[id];
+            }
+        }
+
+        if (inside) {
+            // ---- heat flux divergence (eq. heat-equation), per-face conductivity, lambda pre-scaled by 1/(2h^2)
             T div = T(0);
             if constexpr (MODEL != M_MICRO) {
                 const T t_xm = s_th[b][ty + 1][tx], t_xp = s_th[b][ty + 1][tx + 2];
                 const T t_ym = s_th[b][ty][tx + 1], t_yp = s_th[b][ty + 2][tx + 1];
                 const T l_xm = s_lam[b][ty + 1][tx], l_xp = s_lam[b][ty + 1][tx + 2];
                 const T l_ym = s_lam[b][ty][tx + 1], l_yp = s_lam[b][ty + 2][tx + 1];
-                if (!cf.harmonic) {
-                    div = (lamc + l_xm) * (t_xm - thc) + (lamc + l_xp) * (t_xp - thc) +
-                          (lamc + l_ym) * (t_ym - thc) + (lamc + l_yp) * (t_yp - thc) +
-                          (lamc + lamm) * (thm - thc) + (lamc + lamp) * (thp - thc);
-                    div *= c.half_inv_h2;
+                if (!a.cf.harmonic) {
+                    div = (lamc + l_xm) * (t_xm - thc);
+                    div = FMA(lamc + l_xp, t_xp - thc, div);
+                    div = FMA(lamc + l_ym, t_ym - thc, div);
+                    div = FMA(lamc + l_yp, t_yp - thc, div);
+                    div = FMA(lamc + lamm, thm - thc, div);
+                    div = FMA(lamc + lamp, thp - thc, div);
                 } else {
-                    auto hm = [&](T lj) { T s = lamc + lj; return s > T(0) ? T(2) * lamc * lj / s : T(0); };
-                    div = hm(l_xm) * (t_xm - thc) + hm(l_xp) * (t_xp - thc) + hm(l_ym) * (t_ym - thc) +
-                          hm(l_yp) * (t_yp - thc) + hm(lamm) * (thm - thc) + hm(lamp) * (thp - thc);
-                    div *= c.inv_h2;
+                    auto hm = [&](T lj) {
+                        const T s = lamc + lj;
+                        return positive(s) ? T(4) * lamc * lj / s : T(0);
+                    };
+                    div = hm(l_xm) * (t_xm - thc);
+                    div = FMA(hm(l_xp), t_xp - thc, div);
+                    div = FMA(hm(l_ym), t_ym - thc, div);
+                    div = FMA(hm(l_yp), t_yp - thc, div);
+                    div = FMA(hm(lamm), thm - thc, div);
+                    div = FMA(hm(lamp), thp - thc, div);
                 }
-                int nd = nd_xy;
-                if (cf.dirichlet) nd += ((cf.dirichlet & 16) && k == 0) + ((cf.dirichlet & 32) && k == n3 - 1);
-                if (nd) div += T(nd) * (T(2) * lamc * (th_b - thc) * c.inv_h2);
+                if (dmask) {
+                    const int nd = nd_xy + ((dmask & 16) && k == 0) + ((dmask & 32) && k == n3 - 1);
+                    // Dirichlet face: 2 lambda (theta_b - theta)/h^2 = 4 lambda' (theta_b - theta)
+                    if (nd) div = FMA(T(4 * nd) * lamc, th_b - thc, div);
+                }
             }
-            // ---- Allen-Cahn rate (eq. Allen-Cahn-equation)
+            // ---- Allen-Cahn rate (eq. Allen-Cahn-equation): dphi = W (klap lap + f/2), W = 2 I_W/(alpha xi^2)
             T dph = T(0);
-            if constexpr (MODEL != M_TEMP) {
-                const T IW = water_ind(Gc, c.zeta);
-                if (IW > T(0)) {
+            if constexpr (!TEMP) {
+                const T W = FMA(K.wb, Gc, K.wa);
+                if (positive(W)) {
                     const T p_xm = s_ph[b][ty + 1][tx], p_xp = s_ph[b][ty + 1][tx + 2];
                     const T p_ym = s_ph[b][ty][tx + 1], p_yp = s_ph[b][ty + 2][tx + 1];
-                    const T lap = ((p_xm - phc) + (p_xp - phc) + (p_ym - phc) + (p_yp - phc) + (phm - phc) +
-                                   (php - phc)) * c.inv_h2;
-                    const T under = -thc;  // T* - T
-                    T f;
+                    const T lsum = ((p_xm + p_xp) + (p_ym + p_yp)) + (phm + php);
+                    const T lap = FMA(T(-6), phc, lsum);
+                    const T om = T(1) - phc;
+                    const T q = phc * om;
+                    T inner = phc - T(0.5);
+                    T fh;
                     if constexpr (RX == R_GRADP) {
                         const T gx = p_xp - p_xm, gy = p_yp - p_ym, gz = php - phm;
-                        f = T(2) * phc * (T(1) - phc) * (phc - T(0.5)) +
-                            c.kgrad * dsqrt(gx * gx + gy * gy + gz * gz) * under;
+                        const T gn = dsqrt(FMA(gx, gx, FMA(gy, gy, gz * gz)));
+                        fh = FMA(q, inner, K.kgrad * gn * (-thc));          // eq. (reaction-term-GradP) / 2
                     } else {
-                        const T S = sigma_lim(phc, c.eps0, c.eps1, c.inv_de) *
-                                    sigma_lim(T(1) - phc, c.eps0, c.eps1, c.inv_de);
-                        f = T(2) * phc * (T(1) - phc) * (phc - T(0.5) + c.ksig * S * under);
+                        if (!le_nonneg(phc, K.eps0) && !le_nonneg(om, K.eps0)) {
+                            const T S = sigma_lim(phc, K) * sigma_lim(om, K);
+                            inner = FMA(K.ksig * S, -thc, inner);            // eq. (reaction-term-SigmaP1-P) / 2
+                        }
+                        fh = q * inner;
                     }
-                    dph = IW * (c.xi2 * lap + f) * c.inv_axi2;
+                    dph = W * FMA(K.klap, lap, fh);
                 }
             }
             // ---- latent-heat coupling
             T dth = T(0);
             if constexpr (MODEL == M_FULL) {
-                const T rho = blend(Gc, phc, c.rhoL, c.rhoI, c.rhoG);
-                const T cp = blend(Gc, phc, c.cL, c.cI, c.cG);
-                dth = (div + rho * c.latent * dph) / (rho * cp);
-            } else if constexpr (MODEL == M_TEMP) {
-                const T rho = blend(Gc, phc, c.rhoL, c.rhoI, c.rhoG);
-                const T cp = blend(Gc, phc, c.cL, c.cI, c.cG);
-                const T tg = dtanh(c.gamma * thc);
-                const T dp = T(-0.5) * water_ind(Gc, c.zeta) * c.gamma * (T(1) - tg * tg);
-                dth = div / (rho * (cp - c.latent * dp));
-                dph = dp * dth;  // eq. after (combined-heat-xfer-phase-transition)
+                const T rho = blend3(Gc, phc, K.rhoL, K.dRG, K.dRI);
+                const T cp = blend3(Gc, phc, K.capL, K.dCG, K.dCI);
+                dth = FMA(rho * K.latent, dph, div) * recip_pos(rho * cp);
+            } else if constexpr (TEMP) {
+                const T rho = blend3(Gc, phc, K.rhoL, K.dRG, K.dRI);
+                const T cp = blend3(Gc, phc, K.capL, K.dCG, K.dCI);
+                const T dp = T(-0.5) * water_ind(Gc, K.zeta) * K.gamma * FMA(-tgc, tgc, T(1));
+                dth = div * recip_pos(rho * FMA(-K.latent, dp, cp));  // eq. (combined-heat-xfer-phase-transition)
+                dph = dp * dth;
             }
 
             // ---- fused stage combination
@@ -264,75 +362,92 @@ stage_kernel(const StageArgs<T> a) {
                 if (a.out_th) a.out_th[id] = dth;
                 if (a.out_ph) a.out_ph[id] = dph;
             } else if constexpr (STAGE == 1) {
-                if constexpr (HAS_TH) { a.k1_th[id] = dth; a.ua_th[id] = thc + c13 * dth; }
-                if constexpr (HAS_PH) { a.k1_ph[id] = dph; a.ua_ph[id] = phc + c13 * dph; }
+                if constexpr (HAS_TH) { a.k1_th[id] = dth; a.ua_th[id] = FMA(sc[0], dth, thc); }
+                if constexpr (HAS_PH) { a.k1_ph[id] = dph; a.ua_ph[id] = FMA(sc[0], dph, phc); }
             } else if constexpr (STAGE == 2) {
                 if constexpr (F32) {
-                    if constexpr (HAS_TH) a.ub_th[id] = thc + c16 * (dth - a.k1_th[id]);
-                    if constexpr (HAS_PH) a.ub_ph[id] = phc + c16 * (dph - a.k1_ph[id]);
+                    if constexpr (HAS_TH) a.ub_th[id] = FMA(sc[1], dth - k1t, thc);
+                    if constexpr (HAS_PH) a.ub_ph[id] = FMA(sc[1], dph - k1p, phc);
                 } else {
-                    if constexpr (HAS_TH) a.ub_th[id] = T(a.y_th[cur][id]) + c16 * (a.k1_th[id] + dth);
-                    if constexpr (HAS_PH) a.ub_ph[id] = T(a.y_ph[cur][id]) + c16 * (a.k1_ph[id] + dph);
+                    if constexpr (HAS_TH) a.ub_th[id] = FMA(sc[1], k1t + dth, y_t);
+                    if constexpr (HAS_PH) a.ub_ph[id] = FMA(sc[1], k1p + dph, y_p);
                 }
             } else if constexpr (STAGE == 3) {
                 if constexpr (F32) {
-                    if constexpr (HAS_TH) { a.k3_th[id] = dth; a.ua_th[id] = a.ua_th[id] - c524 * a.k1_th[id] + c38 * dth; }
-                    if constexpr (HAS_PH) { a.k3_ph[id] = dph; a.ua_ph[id] = a.ua_ph[id] - c524 * a.k1_ph[id] + c38 * dph; }
+                    if constexpr (HAS_TH) { a.k3_th[id] = dth; a.ua_th[id] = FMA(sc[3], dth, FMA(-sc[8], k1t, ua_t)); }
+                    if constexpr (HAS_PH) { a.k3_ph[id] = dph; a.ua_ph[id] = FMA(sc[3], dph, FMA(-sc[8], k1p, ua_p)); }
                 } else {
-                    if constexpr (HAS_TH) { a.k3_th[id] = dth; a.ua_th[id] = T(a.y_th[cur][id]) + c18 * a.k1_th[id] + c38 * dth; }
-                    if constexpr (HAS_PH) { a.k3_ph[id] = dph; a.ua_ph[id] = T(a.y_ph[cur][id]) + c18 * a.k1_ph[id] + c38 * dph; }
+                    if constexpr (HAS_TH) { a.k3_th[id] = dth; a.ua_th[id] = FMA(sc[3], dth, FMA(sc[2], k1t, y_t)); }
+                    if constexpr (HAS_PH) { a.k3_ph[id] = dph; a.ua_ph[id] = FMA(sc[3], dph, FMA(sc[2], k1p, y_p)); }
                 }
             } else if constexpr (STAGE == 4) {
                 if constexpr (F32) {
-                    if constexpr (HAS_TH) { a.k4_th[id] = dth; a.ub_th[id] = thc + c38 * a.k1_th[id] - c158 * a.k3_th[id] + c2 * dth; }
-                    if constexpr (HAS_PH) { a.k4_ph[id] = dph; a.ub_ph[id] = phc + c38 * a.k1_ph[id] - c158 * a.k3_ph[id] + c2 * dph; }
+                    if constexpr (HAS_TH) { a.k4_th[id] = dth; a.ub_th[id] = FMA(sc[6], dth, FMA(-sc[9], k3t, FMA(sc[3], k1t, thc))); }
+                    if constexpr (HAS_PH) { a.k4_ph[id] = dph; a.ub_ph[id] = FMA(sc[6], dph, FMA(-sc[9], k3p, FMA(sc[3], k1p, phc))); }
                 } else {
-                    if constexpr (HAS_TH) { a.k4_th[id] = dth; a.ub_th[id] = T(a.y_th[cur][id]) + c12 * a.k1_th[id] - c32 * a.k3_th[id] + c2 * dth; }
-                    if constexpr (HAS_PH) { a.k4_ph[id] = dph; a.ub_ph[id] = T(a.y_ph[cur][id]) + c12 * a.k1_ph[id] - c32 * a.k3_ph[id] + c2 * dph; }
+                    if constexpr (HAS_TH) { a.k4_th[id] = dth; a.ub_th[id] = FMA(sc[6], dth, FMA(-sc[5], k3t, FMA(sc[4], k1t, y_t))); }
+                    if constexpr (HAS_PH) { a.k4_ph[id] = dph; a.ub_ph[id] = FMA(sc[6], dph, FMA(-sc[5], k3p, FMA(sc[4], k1p, y_p))); }
                 }
             } else {  // STAGE 5
                 if constexpr (HAS_TH) {
-                    const T k1 = a.k1_th[id], k3 = a.k3_th[id], k4 = a.k4_th[id];
-                    if constexpr (F32) a.yo_th[cur ^ 1][id] = a.y_th[cur][id] + double(c16 * (k1 + T(4) * k4 + dth));
-                    else a.yo_th[cur ^ 1][id] = a.y_th[cur][id] + c16 * (k1 + T(4) * k4 + dth);
-                    const T e = fabs(c30 * (T(2) * k1 - T(9) * k3 + T(8) * k4 - dth));
-                    if (!(e < T(INFINITY))) nonfinite = true; else emax = e > emax ? e : emax;
+                    const T inc = sc[1] * (k1t + FMA(T(4), k4t, dth));
+                    a.yo_th[cur ^ 1][id] = y_t64 + double(inc);
+                    const unsigned long long eb = abs_bits(sc[7] * FMA(T(2), k1t, FMA(T(-9), k3t, FMA(T(8), k4t, -dth))));
+                    ebits = eb > ebits ? eb : ebits;
                 }
                 if constexpr (HAS_PH) {
-                    const T k1 = a.k1_ph[id], k3 = a.k3_ph[id], k4 = a.k4_ph[id];
-                    if constexpr (F32) a.yo_ph[cur ^ 1][id] = a.y_ph[cur][id] + double(c16 * (k1 + T(4) * k4 + dph));
-                    else a.yo_ph[cur ^ 1][id] = a.y_ph[cur][id] + c16 * (k1 + T(4) * k4 + dph);
-                    const T e = fabs(c30 * (T(2) * k1 - T(9) * k3 + T(8) * k4 - dph));
-                    if (!(e < T(INFINITY))) nonfinite = true; else emax = e > emax ? e : emax;
+                    const T inc = sc[1] * (k1p + FMA(T(4), k4p, dph));
+                    a.yo_ph[cur ^ 1][id] = y_p64 + double(inc);
+                    const unsigned long long eb = abs_bits(sc[7] * FMA(T(2), k1p, FMA(T(-9), k3p, FMA(T(8), k4p, -dph))));
+                    ebits = eb > ebits ? eb : ebits;
                 }
             }
         }
-        thm = thc; phm = phc; lamm = lamc; Gm = Gc;
-        thc = thp; phc = php; lamc = lamp; Gc = Gp;
+
+        // 3. finish plane k+2 into the ring slot of plane k-1; rotate the own column
+        const int b2 = (b + 2) % 3;
+        {
+            T lam2, tg2 = T(0);
+            finish(rth, rph, rG, lam2, tg2);
+            put(b2, ty + 1, tx + 1, rth, rph, lam2);
+            thm = thc; phm = phc; lamm = lamc; tgm = tgc;
+            thc = thp; phc = php; lamc = lamp; Gc = Gp; tgc = tgp;
+            thp = rth; php = rph; lamp = lam2; Gp = rG; tgp = tg2;
+        }
+        if (hal) {
+            T h_lam, h_tg;
+            finish(qth, qph, qG, h_lam, h_tg);
+            put(b2, hy + 1, hx + 1, qth, qph, h_lam);
+        }
+        b = (b + 1) % 3;
         __syncthreads();
     }
 
     if constexpr (STAGE == 5) {
-        // block max of the error estimate -> one atomicMax on the bit pattern (valid for E >= 0)
-        double e = nonfinite ? double(INFINITY) : double(emax);
+        // block max of the error estimate -> one atomicMax on the binary64 bit pattern (valid for E >= 0)
+        unsigned long long e = ebits;
+        if constexpr (F32) {
+            const unsigned fb = (unsigned)ebits;
+            e = (fb >= 0x7F800000u) ? 0x7FF0000000000000ULL
+                                    : (unsigned long long)__double_as_longlong((double)__uint_as_float(fb));
+        }
         for (int o = 16; o > 0; o >>= 1) {
-            double v = __shfl_xor_sync(0xffffffffu, e, o);
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, e, o);
             e = v > e ? v : e;
         }
-        __shared__ double s_red[BY];
+        __shared__ unsigned long long s_red[BY];
         if (tx == 0) s_red[ty] = e;
         __syncthreads();
         if (ty == 0) {
-            double v = tx < BY ? s_red[tx] : 0.0;
+            unsigned long long v = tx < BY ? s_red[tx] : 0ULL;
             for (int o = 16; o > 0; o >>= 1) {
-                double w = __shfl_xor_sync(0xffffffffu, v, o);
+                const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
                 v = w > v ? w : v;
             }
-            if (tx == 0 && v > 0.0)
-                atomicMax(&ctrl->err_bits, (unsigned long long)__double_as_longlong(v));
+            if (tx == 0 && v > 0ULL) atomicMax(&ctrl->err_bits, v);
         }
     }
-    (void)Gm;
+    (void)tgm;
 }
 
 }  // namespace pfgb
