@@ -53,6 +53,10 @@ BYTES_F32 = [36, 28, 44, 44, 68]            # sum 220 = 44 B per cell-stage
 # (blends 6+6+6, fluxes 24, Allen-Cahn 16, latent coupling 6) plus each stage's combination.
 FLOPS_RHS = 64
 FLOPS_COMB = [4, 6, 8, 12, 24]
+# DRAM traffic per cell of the binary64 stage-5 kernel from one ncu capture at 192^3
+# (profiles/stage5_f64_full_sigmap1p_192.md): (632.0 + 101.8) MB / 7.08 M cells.  None once the
+# kernel changes until it is captured again.
+TRAFFIC_F64_S5_PER_CELL = (632.0e6 + 101.8e6) / (192 ** 3)
 
 
 def env_int(k, d):
@@ -300,11 +304,15 @@ def main():
     top = int(np.argmax(prof[:5]))
     top_ms = prof[top]
     flops = (FLOPS_RHS + FLOPS_COMB[top]) * w.n_cells
+    fp64_meas, fp32_meas, copy_meas = pf.pf_measure_peaks()
     fp64_peak_tflops = 152 * 2 * 2 * 2.07e9 / 1e12   # 2 FP64 FMA / clk / SM
     achieved_tf = flops / (top_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": f"merson_{stage_names[top]}_full_sigmap1p_f64",
                 "achieved": achieved_tf, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved_tf / fp64_peak_tflops, "traffic": None,
+                "frac": achieved_tf / fp64_peak_tflops,
+                "traffic": (TRAFFIC_F64_S5_PER_CELL * w.n_cells if (top == 4 and TRAFFIC_F64_S5_PER_CELL) else None),
+                "peak_measured_fp64_tflops": fp64_meas, "frac_of_measured": achieved_tf / fp64_meas,
+                "measured_fp32_tflops": fp32_meas, "measured_copy_gbs": copy_meas,
                 "algorithmic_per_launch": {"flops": flops, "bytes": BYTES_F64[top] * w.n_cells},
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (binary64 pipe)",
                 "hbm_achieved_gbs": BYTES_F64[top] * w.n_cells / (top_ms * 1e-3) / 1e9,

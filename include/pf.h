@@ -166,6 +166,12 @@ pf_status pf_max_phase_rate(pf_grid* g, double* max_rate);
  * advances by n_attempts steps.  Synchronises. */
 pf_status pf_profile_stages(pf_grid* g, int n_attempts, double* stage_ms);
 
+/* Throughput probes of the current device: binary64 and binary32 FMA rates (TFLOP/s, FMA = 2 flops,
+ * 8 independent chains per thread, 8 blocks of 256 threads per SM) and device-memory copy bandwidth
+ * (GB/s, read + write bytes of a 2 x 2 GiB copy, best of 5).  Any pointer may be NULL to skip a probe.
+ * They give the roofline denominators of the stage kernels.  Allocates and frees its own buffers. */
+pf_status pf_measure_peaks(double* fp64_tflops, double* fp32_tflops, double* copy_gbs);
+
 /* Unfrozen-water counts that allocate nothing (no counterpart in the paper; a service for callers).
  *
  * Some callers cannot call cudaMalloc: a plug-in inside a host application that owns all device

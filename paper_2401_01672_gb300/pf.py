@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "PF_OK", -1: "PF_E_INVALID", -2: "PF_E_CUDA", -3: "PF_E_OOM",
 # Every symbol declared in include/pf.h (checked by the CPU tests).
 EXPORTS = ["pf_create_grid", "pf_destroy_grid", "pf_set_geometry", "pf_set_glass", "pf_get_glass", "pf_set_state",
            "pf_get_state", "pf_rhs", "pf_rkm_step", "pf_run_to", "pf_run_fixed", "pf_unfrozen_fraction",
-           "pf_max_phase_rate", "pf_profile_stages", "pf_unfrozen_fraction_noalloc", "pf_last_error",
+           "pf_max_phase_rate", "pf_profile_stages", "pf_measure_peaks", "pf_unfrozen_fraction_noalloc", "pf_last_error",
            "pf_kernel_launches"]
 
 
@@ -82,6 +82,7 @@ def load_library(path: str = LIB_PATH):
         "pf_unfrozen_fraction": [vp, vp, pd, pll, pll, pd],
         "pf_max_phase_rate": [vp, pd],
         "pf_profile_stages": [vp, i, pd],
+        "pf_measure_peaks": [pd, pd, pd],
         "pf_unfrozen_fraction_noalloc": [vp, vp, i, i, i, vp, vp, pd, pll, pll, pd],
     }
     for name, args in sig.items():
@@ -314,6 +315,16 @@ def pf_max_phase_rate(g):
 
 def pf_profile_stages(g, n_attempts):
     return g.profile_stages(n_attempts)
+
+
+def pf_measure_peaks():
+    """(fp64 TFLOP/s, fp32 TFLOP/s, copy GB/s) measured on the current device."""
+    lib = load_library()
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    st = lib.pf_measure_peaks(C.byref(a), C.byref(b), C.byref(c))
+    if st != PF_OK:
+        raise PfError(st, "pf_measure_peaks failed")
+    return a.value, b.value, c.value
 
 
 def pf_unfrozen_fraction_noalloc(G_dev, phi_dev, shape, region=None, stream=None):

@@ -1,0 +1,108 @@
+"""Binary32-field form (stage buffers, slopes and glass field in binary32; state, state update,
+error norm, step control and unfrozen-water sums in binary64) against the FP64 oracle.
+
+Bars: max|phi_f32 - phi_oracle| <= 1e-3 and unfrozen-water fraction within 0.5 % relative after a
+freeze-then-thaw cycle on a bead crop shaped like the 512^3 lognormal-bead workload; the binary64
+path on the same run stays at the oracle's accepted/rejected step counts.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2401_01672_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_01672_gb300 import build
+    build.build()
+    import oracle
+    oracle.build()
+    from paper_2401_01672_gb300 import pf
+    return torch, pf, oracle
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.mark.parametrize("model,rx", [(I.MODEL_FULL, I.REACT_SIGMAP1P), (I.MODEL_FULL, I.REACT_GRADP),
+                                      (I.MODEL_TEMP, I.REACT_SIGMAP1P), (I.MODEL_MICRO, I.REACT_SIGMAP1P)])
+def test_fp32_rhs_against_oracle(env, model, rx):
+    """Right-hand side in binary32 on binary32 inputs: relative to the field maximum the error stays
+    at the level of binary32 rounding of the inputs amplified by the stencil's cancellation."""
+    torch, pf, oracle = env
+    shape = (45, 38, 29)
+    h = 2e-4 if model != I.MODEL_MICRO else 1e-6
+    p = I.default_params(xi=1.3 * h, xi_G=0.4 * h, alpha=4.17e6 if model != I.MODEL_MICRO else 3e9,
+                         dirichlet_faces=I.FACE_ZP, theta_freeze=-5.0, theta_micro=-0.7)
+    th, ph, G = I.random_fields(shape, 77 + model, theta_scale=3.0)
+    # the binary32 form sees binary32-rounded inputs; the oracle gets the same rounded values
+    th32, ph32, G32 = (v.astype(np.float32) for v in (th, ph, G))
+    o = oracle.Oracle(shape, h, model, rx, p)
+    oth, oph = o.rhs(G32.astype(np.float64), th32.astype(np.float64), ph32.astype(np.float64))
+    g = pf.Grid(shape, h, model, rx, I.PREC_FP32, p)
+    g.set_glass(G32.astype(np.float64))
+    dth = torch.empty(g.N, device="cuda", dtype=torch.float32)
+    dph = torch.empty(g.N, device="cuda", dtype=torch.float32)
+    g.rhs(0.0, torch.from_numpy(th32).cuda() if model != I.MODEL_MICRO else None,
+          torch.from_numpy(ph32).cuda() if model != I.MODEL_TEMP else None, dth, dph)
+    torch.cuda.synchronize()
+    if model != I.MODEL_MICRO:
+        assert rel(dth.cpu().numpy(), oth) <= 2e-5
+    if model != I.MODEL_TEMP:
+        assert rel(dph.cpu().numpy(), oph) <= 2e-5
+    g.close()
+
+
+def crop_case(n=48, seed=20240107):
+    """Crop of the lognormal-bead workload at its voxel scale: radii lognormal (mean 12, log-sd 0.25)
+    voxels, Boolean placement to 60 % solid, top face -5 K until t_freeze then +2 K."""
+    shape = (n, n, n)
+    h = 3e-4
+    sv, frac = I.packing_boolean(shape, 0.60, I.lognormal_radius(12.0, 0.25), seed)
+    p = I.default_params(xi=h, xi_G=0.4 * h, alpha=I.ALPHA_MACRO["large"], zeta=2.0, dirichlet_faces=I.FACE_ZP,
+                         theta_freeze=-5.0, theta_thaw=2.0, t_freeze=3.0)
+    th0 = np.full(n ** 3, 1.0)
+    ph0 = I.top_slab_indicator(shape, 2)
+    return shape, h, sv * h, p, th0, ph0
+
+
+def test_fp32_form_freeze_thaw_against_oracle(env):
+    torch, pf, oracle = env
+    shape, h, sp, p, th0, ph0 = crop_case()
+    tol, t_end = 1e-6, 6.0
+    o = oracle.Oracle(shape, h, I.MODEL_FULL, I.REACT_SIGMAP1P, p)
+    G = o.glass(sp, p["xi_G"])
+    ref = o.run(G, th0, ph0, 0.0, 0.01, t_end, tol, 200000)
+    assert ref["status"] == 0 and ref["t"] == t_end
+    u_ref = o.uwc(G, ref["phi"])
+    out = {}
+    for prec in (I.PREC_FP64, I.PREC_FP32):
+        g = pf.Grid(shape, h, I.MODEL_FULL, I.REACT_SIGMAP1P, prec, p)
+        g.set_geometry(sp)
+        g.set_state(th0, ph0, 0.0, 0.01)
+        s = g.run_to(t_end, tol, 200000)
+        gth, gph, t, _ = g.get_state()
+        out[prec] = (s, gth, gph, g.unfrozen_fraction())
+        g.close()
+    s64, th64, ph64, u64 = out[I.PREC_FP64]
+    assert (s64["n_accepted"], s64["n_rejected"]) == (ref["n_accepted"], ref["n_rejected"])
+    assert rel(ph64, ref["phi"]) <= 1e-8 and rel(th64, ref["theta"]) <= 1e-8
+    s32, th32, ph32, u32 = out[I.PREC_FP32]
+    dphi = float(np.max(np.abs(ph32 - ref["phi"])))
+    duwc = abs(u32["uwc"] - u_ref["uwc"]) / max(abs(u_ref["uwc"]), 1e-300)
+    dth = float(np.max(np.abs(th32 - ref["theta"])))
+    print(f"\nfp32 form vs oracle: max|dphi| = {dphi:.3e}, uwc rel = {duwc:.3e}, max|dtheta| = {dth:.3e} K, "
+          f"steps fp32 {s32['n_accepted']}/{s32['n_rejected']} oracle {ref['n_accepted']}/{ref['n_rejected']}, "
+          f"uwc = {u_ref['uwc']:.6f}")
+    # the run must actually freeze something and thaw some of it back
+    assert 0.0 < u_ref["uwc"] < 1.0 and u_ref["n_ice"] > 100
+    assert dphi <= 1e-3
+    assert duwc <= 5e-3
