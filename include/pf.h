@@ -166,6 +166,45 @@ pf_status pf_max_phase_rate(pf_grid* g, double* max_rate);
  * advances by n_attempts steps.  Synchronises. */
 pf_status pf_profile_stages(pf_grid* g, int n_attempts, double* stage_ms);
 
+/* Tile shape of the stage kernels: blocks of 32 x by threads (by = 4, 8 or 16) marching along z over
+ * zc >= 1 planes.  Any shape gives the same results; only speed changes.  Default 8 x 32. */
+pf_status pf_set_tiles(pf_grid* g, int by, int zc);
+pf_status pf_get_tiles(pf_grid* g, int* by, int* zc);
+
+/* Tile autotuner: times the right-hand-side kernel for by in {4, 8, 16} x zc in {4, 8, 16, 32, 64} on
+ * the grid itself (state unchanged) and keeps the fastest.  cache_path (NULL = none) is a text file of
+ * lines "n1xn2xn3/model/reaction/precision by zc ms"; a cached shape is reused without timing and new
+ * results are appended.  Outputs may be NULL. */
+pf_status pf_autotune(pf_grid* g, const char* cache_path, int* by, int* zc, double* ms);
+
+/* ---- Batched persistent runs (independent instances, each with its own adaptive step).
+ * A batch takes ownership of n grids (1 <= n <= 256) that share model, reaction and precision but may
+ * differ in size, parameters, geometry and state; pf_batch_destroy destroys them.  All work goes to
+ * the first grid's stream.  pf_batch_run_to advances every instance to its own t_end[i] (or until its
+ * stage-1 rate max |dphi/dt| <= eq_rate[i], when eq_rate is not NULL and eq_rate[i] > 0, or until
+ * max_steps attempts) in ONE launch of a CUDA graph whose WHILE node repeats, on the device, five
+ * batched persistent stage kernels (a fixed grid of blocks walking the tiles of all active instances),
+ * the per-instance step control and the rebuild of the active-tile list; the loop stops when no
+ * instance is active (at most max_steps + 1 iterations).  Per-instance results in res[n] (may be NULL).
+ * Use pf_batch_grid to read an instance's state afterwards. */
+typedef struct pf_batch pf_batch;
+typedef struct pf_batch_result {
+    pf_run_stats stats;
+    double t_eq;       /* time at which the equilibrium test held (NaN if it did not) */
+    int equilibrium;   /* 1 if the run stopped on the equilibrium test */
+    int status;        /* PF_OK, PF_E_DT_UNDERFLOW or PF_E_NONFINITE for this instance */
+} pf_batch_result;
+pf_status pf_batch_create(int n, pf_grid* const* grids, pf_batch** out);
+pf_status pf_batch_destroy(pf_batch* b);
+pf_grid* pf_batch_grid(pf_batch* b, int i);
+/* One block height for all instances (minimising the summed best times), then the best zc per instance. */
+pf_status pf_batch_autotune(pf_batch* b, const char* cache_path);
+pf_status pf_batch_run_to(pf_batch* b, const double* t_end, const double* eq_rate, double tol, long long max_steps,
+                          pf_batch_result* res);
+/* Device-side loop iterations of the last pf_batch_run_to (steps of the slowest instance + 1). */
+long long pf_batch_iterations(const pf_batch* b);
+const char* pf_batch_last_error(const pf_batch* b);
+
 /* Throughput probes of the current device: binary64 and binary32 FMA rates (TFLOP/s, FMA = 2 flops,
  * 8 independent chains per thread, 8 blocks of 256 threads per SM) and device-memory copy bandwidth
  * (GB/s, read + write bytes of a 2 x 2 GiB copy, best of 5).  Any pointer may be NULL to skip a probe.

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <array>
 #include <vector>
 
 using namespace pfgb;
@@ -144,14 +145,24 @@ __global__ void k_temp_phi(const double* __restrict__ th, const double* __restri
     }
 }
 
-// Step control after stage 5 (one thread).  Accept iff E <= tol (or fixed mode); proposal
-// dt * min(5, 0.8 (tol/E)^(1/5)) capped at dt_max; the next step is shortened to land on
-// t_freeze or t_end.
-__global__ void k_controller(Ctrl* c) {
-    if (threadIdx.x != 0 || blockIdx.x != 0 || c->done) return;
+// Step control after stage 5 (one thread per grid).  Accept iff E <= tol (or fixed mode); proposal
+// dt * min(5, 0.8 (tol/E)^(1/5)) capped at dt_max; the next step is shortened to land on t_freeze or
+// t_end.  With eq_rate > 0 the run stops, before accepting, at the first state whose stage-1 rate
+// max |dphi/dt| is <= eq_rate (the state is then the one at t_eq = t).
+__device__ void controller_step(Ctrl* c) {
+    if (c->done) return;
     const double E = __longlong_as_double((long long)c->err_bits);
+    const double rate = __longlong_as_double((long long)c->rate_bits);
     c->err_bits = 0ULL;
+    c->rate_bits = 0ULL;
     c->last_err = E;
+    if (c->eq_rate > 0.0 && rate <= c->eq_rate) {
+        c->equilibrium = 1;
+        c->t_eq = c->t;
+        c->accepted = 0;
+        c->done = 1;
+        return;
+    }
     const bool finite = E <= DBL_MAX;
     const bool accept = c->fixed || (finite && E <= c->tol);
     c->accepted = accept;
@@ -200,6 +211,37 @@ __global__ void k_controller(Ctrl* c) {
         c->land = 0;
     }
     prepare_step(c);
+}
+
+__global__ void k_controller(Ctrl* c) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) controller_step(c);
+}
+
+// Batched step control: one thread per active instance.
+__global__ void k_batch_controller(Ctrl* const* ctrls, const BatchPlan* plan) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < plan->nactive) controller_step(ctrls[plan->inst[s]]);
+}
+
+// Rebuild the batched work list from the instances' done flags and decide whether the device-side
+// loop runs another step (at most max_iter steps, so the loop always ends).
+__global__ void k_batch_plan(Ctrl* const* ctrls, const int4* tilegrid, int n, BatchPlan* plan,
+                             cudaGraphConditionalHandle cond) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int nt = 0, na = 0;
+    for (int q = 0; q < n; ++q) {
+        if (!ctrls[q]->done) {
+            plan->inst[na] = q;
+            plan->tile_start[na] = nt;
+            nt += tilegrid[q].w;
+            ++na;
+        }
+    }
+    plan->tile_start[na] = nt;
+    plan->ntiles = nt;
+    plan->nactive = na;
+    plan->iter += 1;
+    cudaGraphSetConditional(cond, (na > 0 && plan->iter <= plan->max_iter) ? 1u : 0u);
 }
 
 // UWC partial sums over a half-open box; one slot of 4 words per block:
@@ -614,9 +656,12 @@ pf_status pf_set_state(pf_grid* g, const double* theta, const double* phi, doubl
     c->dt = dt;
     c->cur = 0;
     c->err_bits = 0;
+    c->rate_bits = 0;
     c->done = 0;
     c->status = 0;
     c->last_err = 0;
+    c->equilibrium = 0;
+    c->eq_rate = 0.0;
     pf_status s = push_ctrl(g);
     if (s != PF_OK) return s;
     PF_CUDA(g, cudaStreamSynchronize(g->stream));
@@ -687,6 +732,8 @@ pf_status pf_rkm_step(pf_grid* g, double* dt_inout, double tol, int force_accept
     Ctrl* c = g->hctrl;
     c->dt_step = *dt_inout;
     c->dt = *dt_inout;
+    c->eq_rate = 0.0;
+    c->equilibrium = 0;
     c->land = 0;
     prepare_step(c);
     c->done = 0;
@@ -764,6 +811,8 @@ pf_status pf_run_to(pf_grid* g, double t_end, double tol, long long max_steps, p
     c->t_end = t_end;
     c->tol = tol;
     c->fixed = 0;
+    c->eq_rate = 0.0;
+    c->equilibrium = 0;
     c->single = 0;
     c->max_attempts = max_steps;
     c->n_acc = c->n_rej = 0;
@@ -787,6 +836,8 @@ pf_status pf_run_fixed(pf_grid* g, long long n_steps, double dt, pf_run_stats* s
     c->t_end = INFINITY;
     c->tol = 0.0;
     c->fixed = 1;
+    c->eq_rate = 0.0;
+    c->equilibrium = 0;
     c->single = 0;
     c->max_attempts = n_steps;
     c->n_acc = c->n_rej = 0;
@@ -843,6 +894,8 @@ pf_status pf_profile_stages(pf_grid* g, int n_attempts, double* stage_ms) {
     c->fixed = 1;
     c->single = 1;
     c->dt_step = c->dt;
+    c->eq_rate = 0.0;
+    c->equilibrium = 0;
     c->land = 0;
     prepare_step(c);
     c->done = 0;
@@ -924,5 +977,415 @@ pf_status pf_max_phase_rate(pf_grid* g, double* max_rate) {
     PF_CUDA(g, cudaStreamSynchronize(g->stream));
     return PF_OK;
 }
+
+
+// ------------------------------------------------------------------ tiles and autotuning
+
+static pf_status set_tiles_impl(pf_grid* g, int by, int zc) {
+    if (by != 4 && by != 8 && by != 16) return fail(g, PF_E_INVALID, "by must be 4, 8 or 16");
+    if (zc < 1) return fail(g, PF_E_INVALID, "zc must be >= 1");
+    if (by != g->by || zc != g->zc) free_graph(g);
+    g->by = by;
+    g->zc = zc;
+    return PF_OK;
+}
+
+pf_status pf_set_tiles(pf_grid* g, int by, int zc) {
+    if (!g) return fail(nullptr, PF_E_INVALID, "grid is NULL");
+    return set_tiles_impl(g, by, zc);
+}
+
+pf_status pf_get_tiles(pf_grid* g, int* by, int* zc) {
+    if (!g) return fail(nullptr, PF_E_INVALID, "grid is NULL");
+    if (by) *by = g->by;
+    if (zc) *zc = g->zc;
+    return PF_OK;
+}
+
+static const int kTuneBY[3] = {4, 8, 16};
+static const int kTuneZC[5] = {4, 8, 16, 32, 64};
+
+// Time the plain right-hand side (the stage kernels' common body) for every (by, zc) candidate on the
+// grid itself; ms[b][z] = best of 3 launches (infinity for skipped candidates).
+static pf_status tune_table(pf_grid* g, double ms[3][5]) {
+    pf_status s = sync_ctrl_to_host(g);
+    if (s != PF_OK) return s;
+    const int cur = g->hctrl->cur;
+    const int nb = blocks_for(g->N, 256);
+    if (is_f32(g)) {
+        if (has_th(g)) { k_to_f32<<<nb, 256, 0, g->stream>>>(g->y_th[cur], (float*)g->ua_th, g->N); count_launch(); }
+        if (has_ph(g)) { k_to_f32<<<nb, 256, 0, g->stream>>>(g->y_ph[cur], (float*)g->ua_ph, g->N); count_launch(); }
+    }
+    cudaEvent_t e0, e1;
+    PF_CUDA(g, cudaEventCreate(&e0));
+    PF_CUDA(g, cudaEventCreate(&e1));
+    cudaError_t e = cudaSuccess;
+    const int by0 = g->by, zc0 = g->zc;
+    for (int b = 0; b < 3; ++b)
+        for (int z = 0; z < 5; ++z) {
+            ms[b][z] = INFINITY;
+            if (e != cudaSuccess) continue;
+            if (kTuneZC[z] > 2 * g->n3 && z > 0) continue;
+            g->by = kTuneBY[b];
+            g->zc = kTuneZC[z];
+            double best = INFINITY;
+            for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
+                e = cudaEventRecord(e0, g->stream);
+                if (is_f32(g)) {
+                    StageArgs<float> a = make_args<float>(g);
+                    a.in_th = (const float*)g->ua_th; a.in_ph = (const float*)g->ua_ph;
+                    a.out_th = (float*)g->ub_th; a.out_ph = (float*)g->ub_ph;
+                    if (e == cudaSuccess) e = launch_stage_f32(g->model, g->rx, 0, a, g->by, g->stream);
+                } else {
+                    StageArgs<double> a = make_args<double>(g);
+                    a.in_th = g->y_th[cur]; a.in_ph = g->y_ph[cur];
+                    a.out_th = (double*)g->ub_th; a.out_ph = (double*)g->ub_ph;
+                    if (e == cudaSuccess) e = launch_stage_f64(g->model, g->rx, 0, a, g->by, g->stream);
+                }
+                if (e == cudaSuccess) e = cudaEventRecord(e1, g->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float t = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+                if (r > 0 && t < best) best = t;  // first launch is a warm-up
+            }
+            ms[b][z] = best;
+        }
+    g->by = by0;
+    g->zc = zc0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail(g, PF_E_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    return PF_OK;
+}
+
+static std::string tune_key(const pf_grid* g) {
+    char k[128];
+    snprintf(k, sizeof(k), "%dx%dx%d/m%d/r%d/p%d", g->n1, g->n2, g->n3, g->model, g->rx, g->prec);
+    return k;
+}
+
+// cache file: one line per grid shape "key by zc ms"
+static bool cache_lookup(const char* path, const std::string& key, int* by, int* zc, double* ms) {
+    if (!path) return false;
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char k[128];
+    int b, z;
+    double m;
+    bool found = false;
+    while (fscanf(f, "%127s %d %d %lf", k, &b, &z, &m) == 4)
+        if (key == k) { *by = b; *zc = z; *ms = m; found = true; }
+    fclose(f);
+    return found;
+}
+
+static void cache_store(const char* path, const std::string& key, int by, int zc, double ms) {
+    if (!path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d %.6f\n", key.c_str(), by, zc, ms);
+    fclose(f);
+}
+
+pf_status pf_autotune(pf_grid* g, const char* cache_path, int* by_out, int* zc_out, double* ms_out) {
+    if (!g) return fail(nullptr, PF_E_INVALID, "grid is NULL");
+    int by = 8, zc = 32;
+    double best = INFINITY;
+    const std::string key = tune_key(g);
+    if (!cache_lookup(cache_path, key, &by, &zc, &best)) {
+        double ms[3][5];
+        pf_status s = tune_table(g, ms);
+        if (s != PF_OK) return s;
+        for (int b = 0; b < 3; ++b)
+            for (int z = 0; z < 5; ++z)
+                if (ms[b][z] < best) { best = ms[b][z]; by = kTuneBY[b]; zc = kTuneZC[z]; }
+        cache_store(cache_path, key, by, zc, best);
+    }
+    pf_status s = set_tiles_impl(g, by, zc);
+    if (s != PF_OK) return s;
+    if (by_out) *by_out = by;
+    if (zc_out) *zc_out = zc;
+    if (ms_out) *ms_out = best;
+    return PF_OK;
+}
+
+// ------------------------------------------------------------------ batched persistent runs
+
+struct pf_batch {
+    int n = 0;
+    std::vector<pf_grid*> g;
+    int model = 0, rx = 0, prec = 0, by = 8;
+    cudaStream_t stream = nullptr, cap = nullptr;
+    void* d_args = nullptr;
+    Ctrl** d_ctrls = nullptr;
+    int4* d_tiles = nullptr;
+    BatchPlan* d_plan = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long iters = 0;
+    std::string err;
+};
+
+static pf_status bfail(pf_batch* b, pf_status s, const std::string& m) {
+    if (b) b->err = m;
+    else t_create_err = m;
+    return s;
+}
+
+#define PF_BCUDA(b, call)                                                                              \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) return bfail((b), PF_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static void batch_free_graph(pf_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+}
+
+// per-instance stage arguments and tile lattices on the device
+static pf_status batch_upload(pf_batch* b) {
+    std::vector<int4> tiles(b->n);
+    for (int q = 0; q < b->n; ++q) {
+        pf_grid* g = b->g[q];
+        g->by = b->by;
+        const int nbx = (g->n1 + TX - 1) / TX, nby = (g->n2 + b->by - 1) / b->by, nbz = (g->n3 + g->zc - 1) / g->zc;
+        tiles[q] = make_int4(nbx, nby, nbz, nbx * nby * nbz);
+    }
+    PF_BCUDA(b, cudaMemcpy(b->d_tiles, tiles.data(), sizeof(int4) * b->n, cudaMemcpyHostToDevice));
+    if (b->prec == PF_PREC_FP32_FIELDS) {
+        std::vector<StageArgs<float>> a(b->n);
+        for (int q = 0; q < b->n; ++q) a[q] = make_args<float>(b->g[q]);
+        PF_BCUDA(b, cudaMemcpy(b->d_args, a.data(), sizeof(StageArgs<float>) * b->n, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<StageArgs<double>> a(b->n);
+        for (int q = 0; q < b->n; ++q) a[q] = make_args<double>(b->g[q]);
+        PF_BCUDA(b, cudaMemcpy(b->d_args, a.data(), sizeof(StageArgs<double>) * b->n, cudaMemcpyHostToDevice));
+    }
+    return PF_OK;
+}
+
+static cudaError_t batch_enqueue_step(pf_batch* b, cudaStream_t s, int blocks, cudaGraphConditionalHandle h) {
+    cudaError_t e = cudaSuccess;
+    for (int st = 1; st <= 5 && e == cudaSuccess; ++st) {
+        if (b->prec == PF_PREC_FP32_FIELDS)
+            e = launch_batch_stage_f32(b->model, b->rx, st, (const StageArgs<float>*)b->d_args, b->d_plan, b->d_tiles,
+                                       b->by, blocks, s);
+        else
+            e = launch_batch_stage_f64(b->model, b->rx, st, (const StageArgs<double>*)b->d_args, b->d_plan, b->d_tiles,
+                                       b->by, blocks, s);
+    }
+    if (e != cudaSuccess) return e;
+    k_batch_controller<<<(BATCH_MAX + 127) / 128, 128, 0, s>>>(b->d_ctrls, b->d_plan);
+    k_batch_plan<<<1, 32, 0, s>>>(b->d_ctrls, b->d_tiles, b->n, b->d_plan, h);
+    count_launch(2);
+    return cudaGetLastError();
+}
+
+// Graph: plan -> WHILE(any instance active and iter <= max_iter) { stages 1..5, controller, plan }.
+static pf_status batch_build_graph(pf_batch* b) {
+    batch_free_graph(b);
+    const long long before = pfgb::g_launches.load();
+    cudaGraph_t graph = nullptr;
+    PF_BCUDA(b, cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    // persistent stage grid: enough blocks to fill every SM (the blocks loop over tiles)
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = sms * (2048 / (TX * b->by)) / 2;
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(b->cap, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        k_batch_plan<<<1, 32, 0, b->cap>>>(b->d_ctrls, b->d_tiles, b->n, b->d_plan, h);
+        cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = e2;
+    }
+    cudaGraphNode_t first = nullptr;
+    size_t nn = 1;
+    if (e == cudaSuccess) e = cudaGraphGetNodes(graph, &first, &nn);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, graph, &first, nullptr, 1, &cp);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(b->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = batch_enqueue_step(b, b->cap, blocks, h);
+            cudaError_t e2 = cudaStreamEndCapture(b->cap, &body);
+            e = e1 != cudaSuccess ? e1 : e2;
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    // launches made during capture are recorded, not executed
+    pfgb::g_launches.store(before);
+    if (e != cudaSuccess) {
+        b->exec = nullptr;
+        cudaGetLastError();
+        return bfail(b, PF_E_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    }
+    return PF_OK;
+}
+
+const char* pf_batch_last_error(const pf_batch* b) { return b ? b->err.c_str() : t_create_err.c_str(); }
+
+pf_status pf_batch_destroy(pf_batch* b) {
+    if (!b) return PF_OK;
+    cudaStreamSynchronize(b->stream);
+    batch_free_graph(b);
+    for (pf_grid* g : b->g) pf_destroy_grid(g);
+    if (b->d_args) cudaFree(b->d_args);
+    if (b->d_ctrls) cudaFree(b->d_ctrls);
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    if (b->d_plan) cudaFree(b->d_plan);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+    return PF_OK;
+}
+
+pf_status pf_batch_create(int n, pf_grid* const* grids, pf_batch** out) {
+    if (!out) return bfail(nullptr, PF_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > BATCH_MAX || !grids) return bfail(nullptr, PF_E_INVALID, "need 1..256 grids");
+    for (int q = 0; q < n; ++q) {
+        if (!grids[q]) return bfail(nullptr, PF_E_INVALID, "NULL grid");
+        for (int r = 0; r < q; ++r)
+            if (grids[r] == grids[q]) return bfail(nullptr, PF_E_INVALID, "a grid appears twice");
+        if (grids[q]->model != grids[0]->model || grids[q]->rx != grids[0]->rx || grids[q]->prec != grids[0]->prec)
+            return bfail(nullptr, PF_E_INVALID, "all grids of a batch share model, reaction and precision");
+    }
+    pf_batch* b = new pf_batch();
+    b->n = n;
+    b->g.assign(grids, grids + n);
+    b->model = grids[0]->model;
+    b->rx = grids[0]->rx;
+    b->prec = grids[0]->prec;
+    b->by = grids[0]->by;
+    b->stream = grids[0]->stream;
+    const size_t asz = b->prec == PF_PREC_FP32_FIELDS ? sizeof(StageArgs<float>) : sizeof(StageArgs<double>);
+    bool ok = cudaMalloc(&b->d_args, asz * n) == cudaSuccess;
+    ok = ok && cudaMalloc(&b->d_ctrls, sizeof(Ctrl*) * n) == cudaSuccess;
+    ok = ok && cudaMalloc(&b->d_tiles, sizeof(int4) * n) == cudaSuccess;
+    ok = ok && cudaMalloc(&b->d_plan, sizeof(BatchPlan)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        b->g.clear();
+        pf_batch_destroy(b);
+        return bfail(nullptr, PF_E_OOM, "batch allocation failed");
+    }
+    std::vector<Ctrl*> c(n);
+    for (int q = 0; q < n; ++q) c[q] = grids[q]->dctrl;
+    if (cudaMemcpy(b->d_ctrls, c.data(), sizeof(Ctrl*) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        b->g.clear();
+        pf_batch_destroy(b);
+        return bfail(nullptr, PF_E_CUDA, "batch initialisation failed");
+    }
+    for (int q = 0; q < n; ++q) cudaStreamSynchronize(grids[q]->stream);
+    pf_status s = batch_upload(b);
+    if (s != PF_OK) {
+        std::string m = b->err;
+        b->g.clear();
+        pf_batch_destroy(b);
+        return bfail(nullptr, s, m);
+    }
+    *out = b;
+    return PF_OK;
+}
+
+pf_grid* pf_batch_grid(pf_batch* b, int i) { return (b && i >= 0 && i < b->n) ? b->g[i] : nullptr; }
+
+pf_status pf_batch_autotune(pf_batch* b, const char* cache_path) {
+    if (!b) return bfail(nullptr, PF_E_INVALID, "batch is NULL");
+    // a common block height for the batched kernels, then the best z chunk per instance
+    std::vector<std::array<std::array<double, 5>, 3>> t(b->n);
+    double sum[3] = {0, 0, 0};
+    for (int q = 0; q < b->n; ++q) {
+        double ms[3][5];
+        pf_status s = tune_table(b->g[q], ms);
+        if (s != PF_OK) return bfail(b, s, b->g[q]->err);
+        for (int bb = 0; bb < 3; ++bb) {
+            double m = INFINITY;
+            for (int z = 0; z < 5; ++z) { t[q][bb][z] = ms[bb][z]; m = fmin(m, ms[bb][z]); }
+            sum[bb] += m;
+        }
+    }
+    int bb = 0;
+    for (int k = 1; k < 3; ++k) if (sum[k] < sum[bb]) bb = k;
+    b->by = kTuneBY[bb];
+    for (int q = 0; q < b->n; ++q) {
+        int z = 0;
+        for (int k = 1; k < 5; ++k) if (t[q][bb][k] < t[q][bb][z]) z = k;
+        set_tiles_impl(b->g[q], b->by, kTuneZC[z]);
+        cache_store(cache_path, tune_key(b->g[q]), b->by, kTuneZC[z], t[q][bb][z]);
+    }
+    batch_free_graph(b);
+    return batch_upload(b);
+}
+
+pf_status pf_batch_run_to(pf_batch* b, const double* t_end, const double* eq_rate, double tol, long long max_steps,
+                          pf_batch_result* res) {
+    if (!b) return bfail(nullptr, PF_E_INVALID, "batch is NULL");
+    if (!t_end || !(tol > 0) || max_steps < 1) return bfail(b, PF_E_INVALID, "t_end, tol > 0, max_steps >= 1 required");
+    if (max_steps > (1LL << 30)) max_steps = 1LL << 30;
+    for (int q = 0; q < b->n; ++q) {
+        pf_grid* g = b->g[q];
+        PF_BCUDA(b, cudaMemcpy(g->hctrl, g->dctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+        Ctrl* c = g->hctrl;
+        c->t_end = t_end[q];
+        c->tol = tol;
+        c->fixed = 0;
+        c->single = 0;
+        c->max_attempts = max_steps;
+        c->n_acc = c->n_rej = 0;
+        c->status = 0;
+        c->err_bits = 0;
+        c->rate_bits = 0;
+        c->eq_rate = eq_rate ? eq_rate[q] : 0.0;
+        c->equilibrium = 0;
+        c->t_eq = NAN;
+        c->done = (c->t < t_end[q]) ? 0 : 1;
+        if (!c->done) first_step(c);
+        PF_BCUDA(b, cudaMemcpy(g->dctrl, c, sizeof(Ctrl), cudaMemcpyHostToDevice));
+    }
+    BatchPlan hp = {};
+    hp.iter = 0;
+    hp.max_iter = (int)max_steps + 1;
+    PF_BCUDA(b, cudaMemcpyAsync(b->d_plan, &hp, 4 * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    if (!b->exec) {
+        pf_status s = batch_build_graph(b);
+        if (s != PF_OK) return s;
+    }
+    PF_BCUDA(b, cudaGraphLaunch(b->exec, b->stream));
+    PF_BCUDA(b, cudaMemcpyAsync(&hp, b->d_plan, 4 * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    PF_BCUDA(b, cudaStreamSynchronize(b->stream));
+    b->iters = hp.iter;
+    count_launch(1 + 7LL * (hp.iter - 1));  // plan, then 5 stages + controller + plan per iteration
+    for (int q = 0; q < b->n; ++q) {
+        pf_grid* g = b->g[q];
+        PF_BCUDA(b, cudaMemcpy(g->hctrl, g->dctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+        const Ctrl* c = g->hctrl;
+        if (res) {
+            res[q].stats.n_accepted = c->n_acc;
+            res[q].stats.n_rejected = c->n_rej;
+            res[q].stats.t = c->t;
+            res[q].stats.dt = c->dt;
+            res[q].stats.last_err = c->last_err;
+            res[q].stats.launches = 0;
+            res[q].t_eq = c->equilibrium ? c->t_eq : NAN;
+            res[q].equilibrium = c->equilibrium;
+            res[q].status = c->status;
+        }
+    }
+    return PF_OK;
+}
+
+long long pf_batch_iterations(const pf_batch* b) { return b ? b->iters : -1; }
 
 }  // extern "C"

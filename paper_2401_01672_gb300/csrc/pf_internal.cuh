@@ -61,6 +61,11 @@ struct Ctrl {
     float theta_bf;
     int pad1;
     unsigned long long err_bits;  // max of the error estimate over cells (bit pattern of a double >= 0)
+    unsigned long long rate_bits; // max |dphi/dt| of stage 1 (the current state), same encoding
+    double eq_rate;    // stop when max |dphi/dt| <= eq_rate (0 = never)
+    double t_eq;       // time at which the equilibrium test held
+    int equilibrium;   // the equilibrium test stopped the run
+    int pad2;
     long long n_acc, n_rej, max_attempts;
     int cur;           // state buffer holding y
     int land;
@@ -85,6 +90,18 @@ __host__ __device__ inline void prepare_step(Ctrl* c) {
     c->theta_b = (c->t < c->t_freeze) ? c->theta_freeze : c->theta_thaw;
     c->theta_bf = (float)c->theta_b;
 }
+
+// Work list of the batched persistent stage kernels, rebuilt on the device after every step:
+// active instance s covers tiles [tile_start[s], tile_start[s+1]) of the flattened tile list.
+constexpr int BATCH_MAX = 256;
+struct BatchPlan {
+    int ntiles;
+    int nactive;
+    int iter;
+    int max_iter;
+    int inst[BATCH_MAX];
+    int tile_start[BATCH_MAX + 1];
+};
 
 template <typename T>
 struct StageArgs {
@@ -114,6 +131,13 @@ cudaError_t launch_stage_f64(int model, int rx, int stage, const StageArgs<doubl
                              cudaStream_t s);
 cudaError_t launch_stage_f32(int model, int rx, int stage, const StageArgs<float>& a, int by,
                              cudaStream_t s);
+
+cudaError_t launch_batch_stage_f64(int model, int rx, int stage, const StageArgs<double>* args,
+                                   const BatchPlan* plan, const int4* tilegrid, int by, int blocks,
+                                   cudaStream_t s);
+cudaError_t launch_batch_stage_f32(int model, int rx, int stage, const StageArgs<float>* args,
+                                   const BatchPlan* plan, const int4* tilegrid, int by, int blocks,
+                                   cudaStream_t s);
 
 // Launch accounting (process-wide).
 void count_launch(long long n = 1);

@@ -106,9 +106,11 @@ __device__ __forceinline__ unsigned long long abs_bits(T v) {
     }
 }
 
+// One tile (32 x BY columns, one z chunk) of one stage.  (bxi, byi, bzi) is the tile's position in
+// the grid's tile lattice.  Called by the single-grid kernel (one block per tile) and by the batched
+// persistent kernel (blocks loop over the tiles of all active instances).
 template <int MODEL, int RX, typename T, typename TIN, int STAGE, int BY>
-__global__ void __launch_bounds__(TX * BY)
-stage_kernel(const StageArgs<T> a) {
+__device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi, const int byi, const int bzi) {
     static_assert(STAGE == 1 ? std::is_same<TIN, double>::value : std::is_same<TIN, T>::value,
                   "stage 1 reads the binary64 state; other stages read stage buffers");
     constexpr bool HAS_TH = (MODEL != M_MICRO);  // theta integrated
@@ -140,9 +142,9 @@ stage_kernel(const StageArgs<T> a) {
     const CoefT<T>& K = a.k;
     const int n1 = a.cf.n1, n2 = a.cf.n2, n3 = a.cf.n3;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * BY;
+    const int i0 = bxi * TX, j0 = byi * BY;
     const int i = i0 + tx, j = j0 + ty;
-    const int kb = blockIdx.z * a.zc;
+    const int kb = bzi * a.zc;
     const int ke = min(kb + a.zc, n3);
     const bool inside = (i < n1) && (j < n2);
     const long long plane = (long long)n1 * n2;
@@ -247,6 +249,7 @@ stage_kernel(const StageArgs<T> a) {
     __syncthreads();
 
     unsigned long long ebits = 0ULL;  // max |E| as a bit pattern (NaN/Inf sort above every finite value)
+    unsigned long long rbits = 0ULL;  // stage 1: max |dphi/dt| as a bit pattern
     int b = 0;
 
     for (int k = kb; k < ke; ++k) {
@@ -363,7 +366,12 @@ stage_kernel(const StageArgs<T> a) {
                 if (a.out_ph) a.out_ph[id] = dph;
             } else if constexpr (STAGE == 1) {
                 if constexpr (HAS_TH) { a.k1_th[id] = dth; a.ua_th[id] = FMA(sc[0], dth, thc); }
-                if constexpr (HAS_PH) { a.k1_ph[id] = dph; a.ua_ph[id] = FMA(sc[0], dph, phc); }
+                if constexpr (HAS_PH) {
+                    a.k1_ph[id] = dph;
+                    a.ua_ph[id] = FMA(sc[0], dph, phc);
+                    const unsigned long long rb = abs_bits(dph);
+                    rbits = rb > rbits ? rb : rbits;
+                }
             } else if constexpr (STAGE == 2) {
                 if constexpr (F32) {
                     if constexpr (HAS_TH) a.ub_th[id] = FMA(sc[1], dth - k1t, thc);
@@ -423,11 +431,12 @@ stage_kernel(const StageArgs<T> a) {
         __syncthreads();
     }
 
-    if constexpr (STAGE == 5) {
-        // block max of the error estimate -> one atomicMax on the binary64 bit pattern (valid for E >= 0)
-        unsigned long long e = ebits;
+    if constexpr (STAGE == 5 || (STAGE == 1 && HAS_PH)) {
+        // block max of |E| (stage 5) or |dphi/dt| (stage 1) -> one atomicMax on the binary64 bit
+        // pattern (valid for values >= 0; NaN/Inf patterns sort above every finite value)
+        unsigned long long e = (STAGE == 5) ? ebits : rbits;
         if constexpr (F32) {
-            const unsigned fb = (unsigned)ebits;
+            const unsigned fb = (unsigned)e;
             e = (fb >= 0x7F800000u) ? 0x7FF0000000000000ULL
                                     : (unsigned long long)__double_as_longlong((double)__uint_as_float(fb));
         }
@@ -444,10 +453,35 @@ stage_kernel(const StageArgs<T> a) {
                 const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
                 v = w > v ? w : v;
             }
-            if (tx == 0 && v > 0ULL) atomicMax(&ctrl->err_bits, v);
+            if (tx == 0 && v > 0ULL) atomicMax(STAGE == 5 ? &ctrl->err_bits : &ctrl->rate_bits, v);
         }
     }
+    __syncthreads();  // the block may start another tile: shared memory is reused
     (void)tgm;
+}
+
+template <int MODEL, int RX, typename T, typename TIN, int STAGE, int BY>
+__global__ void __launch_bounds__(TX * BY)
+stage_kernel(const StageArgs<T> a) {
+    stage_tile<MODEL, RX, T, TIN, STAGE, BY>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Batched persistent form: a fixed grid of blocks walks, in order, the tiles of the instances
+// listed in the plan (instances that are finished are not listed).
+template <int MODEL, int RX, typename T, typename TIN, int STAGE, int BY>
+__global__ void __launch_bounds__(TX * BY)
+batch_stage_kernel(const StageArgs<T>* __restrict__ args, const BatchPlan* __restrict__ plan,
+                   const int4* __restrict__ tilegrid) {
+    const int nt = plan->ntiles;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        int s = 0;
+        while (t >= plan->tile_start[s + 1]) ++s;
+        const int inst = plan->inst[s];
+        const int local = t - plan->tile_start[s];
+        const int4 tg = tilegrid[inst];
+        stage_tile<MODEL, RX, T, TIN, STAGE, BY>(args[inst], local % tg.x, (local / tg.x) % tg.y,
+                                                  local / (tg.x * tg.y));
+    }
 }
 
 }  // namespace pfgb

@@ -27,7 +27,9 @@ STATUS_NAMES = {0: "PF_OK", -1: "PF_E_INVALID", -2: "PF_E_CUDA", -3: "PF_E_OOM",
 EXPORTS = ["pf_create_grid", "pf_destroy_grid", "pf_set_geometry", "pf_set_glass", "pf_get_glass", "pf_set_state",
            "pf_get_state", "pf_rhs", "pf_rkm_step", "pf_run_to", "pf_run_fixed", "pf_unfrozen_fraction",
            "pf_max_phase_rate", "pf_profile_stages", "pf_measure_peaks", "pf_unfrozen_fraction_noalloc", "pf_last_error",
-           "pf_kernel_launches"]
+           "pf_kernel_launches", "pf_set_tiles", "pf_get_tiles", "pf_autotune", "pf_batch_create",
+           "pf_batch_destroy", "pf_batch_grid", "pf_batch_autotune", "pf_batch_run_to", "pf_batch_iterations",
+           "pf_batch_last_error"]
 
 
 class PfError(RuntimeError):
@@ -52,6 +54,15 @@ class pf_run_stats(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class pf_batch_result(C.Structure):
+    _fields_ = [("stats", pf_run_stats), ("t_eq", C.c_double), ("equilibrium", C.c_int), ("status", C.c_int)]
+
+    def as_dict(self):
+        d = self.stats.as_dict()
+        d.update(t_eq=self.t_eq, equilibrium=bool(self.equilibrium), status=self.status)
+        return d
 
 
 _lib = None
@@ -83,6 +94,13 @@ def load_library(path: str = LIB_PATH):
         "pf_max_phase_rate": [vp, pd],
         "pf_profile_stages": [vp, i, pd],
         "pf_measure_peaks": [pd, pd, pd],
+        "pf_set_tiles": [vp, i, i],
+        "pf_get_tiles": [vp, pi, pi],
+        "pf_autotune": [vp, C.c_char_p, pi, pi, pd],
+        "pf_batch_create": [i, C.POINTER(vp), C.POINTER(vp)],
+        "pf_batch_destroy": [vp],
+        "pf_batch_autotune": [vp, C.c_char_p],
+        "pf_batch_run_to": [vp, pd, pd, d, ll, C.POINTER(pf_batch_result)],
         "pf_unfrozen_fraction_noalloc": [vp, vp, i, i, i, vp, vp, pd, pll, pll, pd],
     }
     for name, args in sig.items():
@@ -93,6 +111,12 @@ def load_library(path: str = LIB_PATH):
     lib.pf_last_error.restype = C.c_char_p
     lib.pf_kernel_launches.argtypes = []
     lib.pf_kernel_launches.restype = C.c_longlong
+    lib.pf_batch_grid.argtypes = [vp, i]
+    lib.pf_batch_grid.restype = vp
+    lib.pf_batch_iterations.argtypes = [vp]
+    lib.pf_batch_iterations.restype = C.c_longlong
+    lib.pf_batch_last_error.argtypes = [vp]
+    lib.pf_batch_last_error.restype = C.c_char_p
     _lib = lib
     return lib
 
@@ -170,9 +194,9 @@ class Grid:
         return torch.float32 if self.precision == _inputs.PREC_FP32 else torch.float64
 
     def close(self):
-        if getattr(self, "handle", None):
+        if getattr(self, "handle", None) and not getattr(self, "_owned_by_batch", False):
             _lib.pf_destroy_grid(self.handle)
-            self.handle = None
+        self.handle = None
 
     def __del__(self):
         try:
@@ -249,6 +273,20 @@ class Grid:
                self.handle)
         return {"uwc": u.value, "n_ice": ni.value, "n_water": nw.value, "smooth": sm.value}
 
+    def set_tiles(self, by, zc):
+        _check(_lib.pf_set_tiles(self.handle, int(by), int(zc)), self.handle)
+
+    def get_tiles(self):
+        by, zc = C.c_int(), C.c_int()
+        _check(_lib.pf_get_tiles(self.handle, C.byref(by), C.byref(zc)), self.handle)
+        return by.value, zc.value
+
+    def autotune(self, cache_path=None):
+        by, zc, ms = C.c_int(), C.c_int(), C.c_double()
+        _check(_lib.pf_autotune(self.handle, cache_path.encode() if cache_path else None, C.byref(by), C.byref(zc),
+                                C.byref(ms)), self.handle)
+        return by.value, zc.value, ms.value
+
     def profile_stages(self, n_attempts):
         out = (C.c_double * 6)()
         _check(_lib.pf_profile_stages(self.handle, int(n_attempts), out), self.handle)
@@ -315,6 +353,69 @@ def pf_max_phase_rate(g):
 
 def pf_profile_stages(g, n_attempts):
     return g.profile_stages(n_attempts)
+
+
+class Batch:
+    """Owning handle of a pf_batch: the grids passed in become batch-owned (their Python handles are
+    detached and must not be used except through Batch.grid_state)."""
+
+    def __init__(self, grids):
+        lib = load_library()
+        self.grids = list(grids)
+        arr = (C.c_void_p * len(self.grids))(*[g.handle for g in self.grids])
+        out = C.c_void_p()
+        st = lib.pf_batch_create(len(self.grids), arr, C.byref(out))
+        if st != PF_OK:
+            msg = lib.pf_batch_last_error(None)
+            raise PfError(st, msg.decode() if msg else "")
+        for g in self.grids:
+            g._owned_by_batch = True
+        self.handle = out
+        self.n = len(self.grids)
+
+    def _check(self, st):
+        if st != PF_OK:
+            msg = _lib.pf_batch_last_error(self.handle)
+            raise PfError(st, msg.decode() if msg else "")
+
+    def autotune(self, cache_path=None):
+        self._check(_lib.pf_batch_autotune(self.handle, cache_path.encode() if cache_path else None))
+        return [g.get_tiles() for g in self.grids]
+
+    def run_to(self, t_end, tol, max_steps, eq_rate=None):
+        te = (C.c_double * self.n)(*[float(v) for v in t_end])
+        er = None if eq_rate is None else (C.c_double * self.n)(*[float(v) for v in eq_rate])
+        res = (pf_batch_result * self.n)()
+        self._check(_lib.pf_batch_run_to(self.handle, te, er, float(tol), int(max_steps), res))
+        return [r.as_dict() for r in res]
+
+    def iterations(self):
+        return _lib.pf_batch_iterations(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.pf_batch_destroy(self.handle)
+            self.handle = None
+            for g in self.grids:
+                g.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pf_batch_create(grids):
+    return Batch(grids)
+
+
+def pf_batch_run_to(b, t_end, tol, max_steps, eq_rate=None):
+    return b.run_to(t_end, tol, max_steps, eq_rate)
+
+
+def pf_autotune(g, cache_path=None):
+    return g.autotune(cache_path)
 
 
 def pf_measure_peaks():
