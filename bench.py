@@ -225,6 +225,37 @@ def time_form(torch, pf, w, precision, steps, warmup, stream):
     return g, s, ms, launches, prof
 
 
+def run_sweep(args, rank, world):
+    """Time-to-solution of the micro-scale sweep: every instance runs to its equilibrium test
+    (4 xi max|dphi/dt| <= 1e-3 mu dT), its t_end = 4 L/(mu dT) or the attempt cap."""
+    from paper_2401_01672_gb300 import sweep
+    inst = I.sweep_instances(args.instances)
+    mine = inst[rank::world]       # instances are independent: shard them over ranks
+    with ClockSampler(env_int("LOCAL_RANK", 0)) as clk:
+        b = sweep.run_batched(mine, max_steps=args.max_steps, keep_phi=True)
+    p = sweep.run_plain(mine, max_steps=args.max_steps, keep_phi=True)
+    acc = sweep.compare(b, p)
+    cells = sum(int(np.prod(i.shape)) for i in mine)
+    att_b = sum(r["n_accepted"] + r["n_rejected"] for r in b["instances"])
+    att_p = sum(r["n_accepted"] + r["n_rejected"] for r in p["instances"])
+    cell_att_b = sum(int(np.prod(i.shape)) * (r["n_accepted"] + r["n_rejected"]) for i, r in zip(mine, b["instances"]))
+    if rank == 0:
+        line = {"metric": "sweep time-to-solution (equilibrium, t_end or cap)", "value": b["wall_s"], "unit": "s",
+                "higher_is_better": False, "n_gpus": world, "steps": args.max_steps, "warmup": 0,
+                "dtype": "f32 fields / f64 control", "data": "synthetic", "scaling": "weak",
+                "config": {"workload": f"micro_sweep_{len(inst)}", "instances": len(mine), "cells": cells,
+                           "sizes": [i.shape[0] for i in mine], "cap": args.max_steps, "tol": 1e-6},
+                "batched": {"wall_s": b["wall_s"], "attempts": att_b, "device_iterations": b["iterations"],
+                            "cell_stage_per_s": 5 * cell_att_b / b["wall_s"],
+                            "equilibrium": sum(r["equilibrium"] for r in b["instances"]),
+                            "tiles_by_zc": b["tiles"][:4]},
+                "plain_fp64": {"wall_s": p["wall_s"], "attempts": att_p,
+                               "equilibrium": sum(r["equilibrium"] for r in p["instances"])},
+                "speedup_vs_plain_fp64": p["wall_s"] / b["wall_s"], "accuracy_vs_plain_fp64": acc,
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -233,6 +264,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-form", action="store_true")
+    ap.add_argument("--workload", default="full256", choices=["full256", "sweep48"],
+                    help="full256: the binary64 bead workload (default); sweep48: the 48-instance micro-scale "
+                         "sweep, batched binary32 persistent run vs the plain binary64 method")
+    ap.add_argument("--max-steps", type=int, default=600, help="sweep48: attempt cap per instance")
+    ap.add_argument("--instances", type=int, default=48, help="sweep48: number of instances")
     ap.add_argument("--size", type=int, default=N_SIDE, help="grid side (256 = the benchmark workload; "
                     "smaller sizes are for profiling captures only)")
     args = ap.parse_args()
@@ -253,6 +289,9 @@ def main():
     from paper_2401_01672_gb300 import pf
 
     torch.cuda.set_device(local)
+    if args.workload == "sweep48":
+        run_sweep(args, rank, world)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -88,13 +88,6 @@ def rng(seed: int) -> np.random.Generator:
 
 
 # ----------------------------------------------------------------- packings
-def _ball_offsets(r: float):
-    """Integer voxel offsets whose centres lie strictly inside a ball of radius r (voxels)."""
-    R = int(math.ceil(r))
-    ax = np.arange(-R, R + 1)
-    return ax
-
-
 def _stamp(mask: np.ndarray, c, r):
     """Mark voxels whose centres are inside the sphere (c, r) (voxel units, centre at i+1/2)."""
     n1, n2, n3 = mask.shape[2], mask.shape[1], mask.shape[0]
@@ -296,3 +289,48 @@ def full_bead_case(n, seed, solid=0.60, r_lo=10.0, r_hi=16.0, radius_sampler=Non
     return Workload(name or f"full_{n}", shape, h, MODEL_FULL, REACT_SIGMAP1P, p, sp, math.nan,
                     theta0, phi0, extra={"solid_fraction_sharp": frac, "tol": 1e-6,
                                          "n_spheres": len(sp)})
+
+
+# Surface-tension scales and supercoolings of the micro-scale parametric sweep.
+SIGMA_SCALES = (1.0, 3.0, 10.0, 30.0, 100.0, 300.0)
+SUPERCOOLINGS = (0.1, 0.2, 0.5, 1.0, 2.0, 5.0, 10.0, 20.0)
+
+
+@dataclass
+class SweepInstance:
+    shape: tuple
+    h: float
+    params: dict
+    spheres: np.ndarray       # metres
+    phi0: np.ndarray
+    dt0: float
+    t_end: float
+    eq_rate: float            # max |dphi/dt| at equilibrium: 4 xi max|dphi/dt| <= 1e-3 mu dT
+    sigma_scale: float
+    dT: float
+
+
+def sweep_instances(n=48, seed=20240108, h=1e-7, solid=0.60, sizes=None, seed_radius=4.0):
+    """Micro-scale parametric sweep: instance i has an n_i^3 grid (n_i = 8 round(12 2^(i/(n-1))), 96..192,
+    in a seeded permutation), its own Boolean packing (radii uniform in [10, 16] voxels, `solid` sharp
+    solid fraction), surface-tension scale s and supercooling dT from the 6 x 8 table (alpha = alpha_Table1 / s),
+    an ice ball of `seed_radius` voxels in the pore space, t_end = 4 L / (mu dT)."""
+    g = rng(seed)
+    if sizes is None:
+        sizes = [8 * int(round(12 * 2 ** (i / max(n - 1, 1)))) for i in range(n)]
+    perm = g.permutation(len(sizes))
+    combos = [(sc, dT) for sc in SIGMA_SCALES for dT in SUPERCOOLINGS]
+    out = []
+    for i in range(n):
+        N = int(sizes[perm[i] % len(sizes)])
+        sc, dT = combos[(i * len(combos)) // n]
+        shape = (N, N, N)
+        sv, _ = packing_boolean(shape, solid, uniform_radius(10.0, 16.0), seed + 1 + i)
+        c = pore_ball_center(shape, sv, seed_radius, seed + 1001 + i, margin=0.5)
+        phi0 = ball_indicator(shape, c, seed_radius)
+        p = default_params(xi=h, xi_G=0.4 * h, zeta=2.0, theta_micro=-dT, alpha=TABLE1["alpha"] / sc)
+        sp = sv.copy()
+        sp *= h
+        out.append(SweepInstance(shape, h, p, sp, phi0, 0.1 * p["alpha"] * h * h, 4 * N * h / (p["mu"] * dT),
+                                 1e-3 * p["mu"] * dT / (4 * h), sc, dT))
+    return out
