@@ -227,7 +227,7 @@ def time_form(torch, pf, w, precision, steps, warmup, stream):
 
 def run_sweep(args, rank, world):
     """Time-to-solution of the micro-scale sweep: every instance runs to its equilibrium test
-    (4 xi max|dphi/dt| <= 1e-3 mu dT), its t_end = 4 L/(mu dT) or the attempt cap."""
+    (ice count unchanged for the time a free front needs to cross 20 cells), its t_end = 4 L/(mu dT) or the attempt cap."""
     from paper_2401_01672_gb300 import sweep
     inst = I.sweep_instances(args.instances)
     mine = inst[rank::world]       # instances are independent: shard them over ranks
@@ -256,6 +256,58 @@ def run_sweep(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_warmstart(args, rank, world):
+    """Learned warm start: equilibria of 64^3 instances from the batched solver -> BF16 encoder-decoder
+    trained with the library's kernels -> inference on larger packings -> binary64 RKM relaxation to the
+    equilibrium test, against the plain binary64 run from the nucleation seed."""
+    import torch
+    from paper_2401_01672_gb300 import warmstart as WS
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    train = I.warmstart_instances(args.train_samples, 64, seed=20240109)
+    t_gen0 = time.perf_counter()
+    G, feat, P, stats = WS.generate(train)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen0
+    t_tr0 = time.perf_counter()
+    net, hist = WS.train(G, feat, P, steps=args.train_steps, batch=4, log_every=max(1, args.train_steps // 10))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t_tr0
+    tests = I.warmstart_instances(args.tests, args.test_side, seed=20240110)
+    rows = []
+    for inst in tests:
+        cold, phi_c, w_c, Gt = WS.relax(inst, inst.phi0)
+        torch.cuda.synchronize()
+        ti = time.perf_counter()
+        phi_pred = WS.predict(net, inst, Gt)
+        torch.cuda.synchronize()
+        t_inf = time.perf_counter() - ti
+        warm, phi_w, w_w, _ = WS.relax(inst, phi_pred)
+        rows.append({"dT": inst.dT, "sigma_scale": inst.sigma_scale,
+                     "cold": {"attempts": cold["n_accepted"] + cold["n_rejected"], "wall_s": w_c,
+                              "equilibrium": cold["equilibrium"], "t_eq": cold["t_eq"], "uwc": cold["uwc"]},
+                     "warm": {"attempts": warm["n_accepted"] + warm["n_rejected"], "wall_s": w_w + t_inf,
+                              "inference_s": t_inf, "equilibrium": warm["equilibrium"], "t_eq": warm["t_eq"],
+                              "uwc": warm["uwc"]},
+                     "max_abs_dphi_warm_vs_cold": float(np.max(np.abs(phi_w - phi_c))),
+                     "max_abs_dphi_prediction_vs_cold": float(np.max(np.abs(phi_pred - phi_c))),
+                     "uwc_rel_diff": abs(warm["uwc"] - cold["uwc"]) / max(abs(cold["uwc"]), 1e-12)})
+    cold_s = sum(r["cold"]["wall_s"] for r in rows)
+    warm_s = sum(r["warm"]["wall_s"] for r in rows)
+    line = {"metric": "time-to-equilibrium, learned warm start + binary64 relaxation vs plain binary64",
+            "value": warm_s, "unit": "s", "higher_is_better": False, "n_gpus": world, "steps": args.train_steps,
+            "warmup": 0, "dtype": "bf16 network (fp32 accumulation), f64 relaxation", "data": "synthetic",
+            "scaling": "weak",
+            "config": {"workload": f"warmstart_64_to_{args.test_side}", "train_samples": args.train_samples,
+                       "train_steps": args.train_steps, "test_side": args.test_side, "tests": args.tests},
+            "plain_fp64_s": cold_s, "speedup_vs_plain_fp64": cold_s / warm_s if warm_s > 0 else None,
+            "data_generation_s": t_gen, "train_s": t_train,
+            "train_equilibria": sum(1 for r in stats if r["equilibrium"]), "loss_history": hist, "tests": rows,
+            "wall_total_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -264,11 +316,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-form", action="store_true")
-    ap.add_argument("--workload", default="full256", choices=["full256", "sweep48"],
+    ap.add_argument("--workload", default="full256", choices=["full256", "sweep48", "warmstart"],
                     help="full256: the binary64 bead workload (default); sweep48: the 48-instance micro-scale "
                          "sweep, batched binary32 persistent run vs the plain binary64 method")
     ap.add_argument("--max-steps", type=int, default=600, help="sweep48: attempt cap per instance")
     ap.add_argument("--instances", type=int, default=48, help="sweep48: number of instances")
+    ap.add_argument("--train-samples", type=int, default=2000, help="warmstart: 64^3 training equilibria")
+    ap.add_argument("--train-steps", type=int, default=1500, help="warmstart: Adam steps")
+    ap.add_argument("--test-side", type=int, default=256, help="warmstart: side of the inference grids")
+    ap.add_argument("--tests", type=int, default=2, help="warmstart: number of inference instances")
     ap.add_argument("--size", type=int, default=N_SIDE, help="grid side (256 = the benchmark workload; "
                     "smaller sizes are for profiling captures only)")
     args = ap.parse_args()
@@ -291,6 +347,9 @@ def main():
     torch.cuda.set_device(local)
     if args.workload == "sweep48":
         run_sweep(args, rank, world)
+        return
+    if args.workload == "warmstart":
+        run_warmstart(args, rank, world)
         return
     dist = None
     if world > 1:

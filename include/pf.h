@@ -178,11 +178,17 @@ pf_status pf_get_tiles(pf_grid* g, int* by, int* zc);
 pf_status pf_autotune(pf_grid* g, const char* cache_path, int* by, int* zc, double* ms);
 
 /* ---- Batched persistent runs (independent instances, each with its own adaptive step).
+ * Equilibrium test (Sec. 3.3: the unfrozen water content no longer changes): stage 1 counts the ice
+ * cells of the pore bulk, #{phi > 1/2 and I_W(G) > 1/2}, of the current state; an instance is in
+ * equilibrium at the first state whose count has stayed within eq_rel_tol x (pore-bulk cells) of a
+ * reference value for eq_window seconds (eq_rel_tol = 0: no change at all).  (The thin glass
+ * layer with I_W -> 0 keeps relaxing on the slow time scale alpha xi^2 / I_W without moving any pore
+ * interface; it is left out of the test but not out of pf_unfrozen_fraction.)
  * A batch takes ownership of n grids (1 <= n <= 256) that share model, reaction and precision but may
  * differ in size, parameters, geometry and state; pf_batch_destroy destroys them.  All work goes to
- * the first grid's stream.  pf_batch_run_to advances every instance to its own t_end[i] (or until its
- * stage-1 rate max |dphi/dt| <= eq_rate[i], when eq_rate is not NULL and eq_rate[i] > 0, or until
- * max_steps attempts) in ONE launch of a CUDA graph whose WHILE node repeats, on the device, five
+ * the first grid's stream.  pf_batch_run_to advances every instance to its own t_end[i] (or until the
+ * equilibrium test holds, when eq_window is not NULL and eq_window[i] > 0, or until max_steps attempts)
+ * in ONE launch of a CUDA graph whose WHILE node repeats, on the device, five
  * batched persistent stage kernels (a fixed grid of blocks walking the tiles of all active instances),
  * the per-instance step control and the rebuild of the active-tile list; the loop stops when no
  * instance is active (at most max_steps + 1 iterations).  Per-instance results in res[n] (may be NULL).
@@ -199,8 +205,8 @@ pf_status pf_batch_destroy(pf_batch* b);
 pf_grid* pf_batch_grid(pf_batch* b, int i);
 /* One block height for all instances (minimising the summed best times), then the best zc per instance. */
 pf_status pf_batch_autotune(pf_batch* b, const char* cache_path);
-pf_status pf_batch_run_to(pf_batch* b, const double* t_end, const double* eq_rate, double tol, long long max_steps,
-                          pf_batch_result* res);
+pf_status pf_batch_run_to(pf_batch* b, const double* t_end, const double* eq_window, double eq_rel_tol, double tol,
+                          long long max_steps, pf_batch_result* res);
 /* Device-side loop iterations of the last pf_batch_run_to (steps of the slowest instance + 1). */
 long long pf_batch_iterations(const pf_batch* b);
 const char* pf_batch_last_error(const pf_batch* b);

@@ -1,0 +1,85 @@
+/*
+ * pfnn.h -- C ABI of the learned warm start's kernels (BF16 tensor-core 3D convolutions and the
+ * encoder-decoder glue), used to train and run a network that predicts the micro-scale equilibrium
+ * phase field from the bead mask, the supercooling and the surface-tension scale.  Its prediction is
+ * the initial state of the Runge-Kutta-Merson relaxation of Secs. 2.4-2.5 (the integration stays the
+ * judge of the result); the network itself is not part of the paper.
+ *
+ * Conventions
+ *   - Activations: N x D x H x W voxels, channels last (NDHWC), bfloat16.  A tensor may be the channel
+ *     slice [off, off + C) of a buffer with ld channels per voxel.  FP32 gradient buffers use the
+ *     same layout.
+ *   - Convolutions: 3x3x3 taps, zero padding 1, stride 1.  Weights [27][Cout][Cin] bfloat16, tap
+ *     t = (dz+1)*9 + (dy+1)*3 + (dx+1).  Products on the tensor cores (mma.sync m16n8k16, bf16 in,
+ *     fp32 accumulation).
+ *   - All pointers are DEVICE pointers borrowed for the call (caller-owned, e.g. torch tensors);
+ *     16-byte alignment of every bf16 row is required (ld, off multiples of 8).  Work is enqueued on
+ *     `stream` (cudaStream_t, NULL = legacy default stream); nothing synchronises.
+ *   - Return PF_OK, PF_E_INVALID for unsupported sizes/alignments (nothing launched) or PF_E_CUDA.
+ */
+#ifndef PFNN_H
+#define PFNN_H
+#include "pf.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Forward (flip = 0): y[v][co] = act(bias[co] + sum_{t,ci} x[v + off(t)][ci] w[t][co][ci]).
+ * Backward data (flip = 1, w = transposed weights [27][Cin][Cout], cin/cout swapped):
+ *   dx[v][ci] = sum_{t,co} dy[v - off(t)][co] w[t][co][ci].
+ * cin a multiple of 16; cout in {8, 16, 32} or any multiple of 8 >= 64; act = ReLU when relu != 0.
+ * Output either bf16 (y_bf16) or fp32 (y_f32; accumulate != 0 adds to it). */
+pf_status pfnn_conv3d(const void* x, int ldx, int xoff, const void* w, int cin, int cout, const float* bias, int relu,
+                      int flip, void* y_bf16, float* y_f32, int ldy, int yoff, int accumulate, int n, int d, int h,
+                      int wd, void* stream);
+
+/* Weight gradient: dw[t][co][ci] += sum_v dy[v][co] x[v + off(t)][ci]  (fp32 atomics, split over voxels). */
+pf_status pfnn_conv3d_wgrad(const void* dy, int lddy, int dyoff, int cout, const void* x, int ldx, int xoff, int cin,
+                            float* dw, int n, int d, int h, int wd, void* stream);
+
+/* db[c] += sum_v dz[v][off + c]  (dz fp32 with ld channels per voxel). */
+pf_status pfnn_bias_grad(const float* dz, int ld, int off, int c, long long nvox, float* db, void* stream);
+
+/* ReLU backward and cast: dz[v][c] = dy[v][off + c] * (y[v][yoff + c] > 0) (y may be NULL: no mask);
+ * dz_f32 (may be NULL) and dz_bf16 are compact [nvox][c]. */
+pf_status pfnn_relu_bwd_cast(const float* dy, int lddy, int dyoff, const void* y, int ldy, int yoff, int c,
+                             long long nvox, float* dz_f32, void* dz_bf16, void* stream);
+
+/* [27][Cout][Cin] -> [27][Cin][Cout] (weights for the backward-data convolution). */
+pf_status pfnn_weight_transpose(const void* w, void* wt, int cout, int cin, void* stream);
+
+/* 2x2x2 average pooling (even D, H, W of the input) and its adjoint (dy compact, dx += strided). */
+pf_status pfnn_avgpool(const void* x, int ldx, int xoff, void* y, int ldy, int yoff, int c, int n, int d, int h, int wd,
+                       void* stream);
+pf_status pfnn_avgpool_bwd(const float* dy, int c, float* dx, int lddx, int dxoff, int n, int d, int h, int wd,
+                           void* stream);
+
+/* x2 nearest-neighbour upsampling (d, h, wd = OUTPUT size) and its adjoint (d, h, wd = coarse size,
+ * dx compact +=). */
+pf_status pfnn_upsample(const void* x, int c, void* y, int ldy, int yoff, int n, int d, int h, int wd, void* stream);
+pf_status pfnn_upsample_bwd(const float* dy, int lddy, int dyoff, int c, float* dx, int n, int d, int h, int wd,
+                            void* stream);
+
+/* 1x1x1 head: logit[v] = b[0] + sum_c x[v][c] w[c] (c <= 32), prob = sigmoid(logit) (may be NULL).  With a
+ * target (fp32, may be NULL): *loss += mean binary cross-entropy, dlogit[v] = (prob - target)/nvox. */
+pf_status pfnn_head_forward(const void* x, int c, const float* w, const float* b, const float* target, long long nvox,
+                            float* prob, float* dlogit, double* loss, void* stream);
+/* dx[v][c] = dlogit[v] w[c] (compact), dw[c] += sum_v dlogit[v] x[v][c], db[0] += sum_v dlogit[v]. */
+pf_status pfnn_head_backward(const void* x, int c, const float* w, const float* dlogit, long long nvox, float* dx,
+                             float* dw, float* db, void* stream);
+
+/* Network input (16 channels, compact): channel 0 = G[v] (fp32 glass field), channels 1..nfeat =
+ * feat[sample][f] (fp32, sample = v / vox_per_sample), the rest 0. */
+pf_status pfnn_pack_input(const float* G, const float* feat, int nfeat, long long vox_per_sample, long long nvox,
+                          void* out, void* stream);
+
+/* Adam step (bias-corrected, step >= 1) on fp32 master weights p with gradient g and moments m, v;
+ * p_bf16 (may be NULL) receives the rounded working copy. */
+pf_status pfnn_adam(float* p, const float* g, float* m, float* v, void* p_bf16, long long n, float lr, float b1,
+                    float b2, float eps, int step, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFNN_H */

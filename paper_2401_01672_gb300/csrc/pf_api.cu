@@ -147,21 +147,29 @@ __global__ void k_temp_phi(const double* __restrict__ th, const double* __restri
 
 // Step control after stage 5 (one thread per grid).  Accept iff E <= tol (or fixed mode); proposal
 // dt * min(5, 0.8 (tol/E)^(1/5)) capped at dt_max; the next step is shortened to land on t_freeze or
-// t_end.  With eq_rate > 0 the run stops, before accepting, at the first state whose stage-1 rate
-// max |dphi/dt| is <= eq_rate (the state is then the one at t_eq = t).
+// t_end.  With eq_window > 0 the run stops, before accepting, once the pore-bulk ice count of the
+// current state (measured in stage 1) has stayed within eq_rel_tol x (pore-bulk cells) of a reference
+// value for eq_window seconds (the state is then the one at t_eq = t).
 __device__ void controller_step(Ctrl* c) {
     if (c->done) return;
     const double E = __longlong_as_double((long long)c->err_bits);
-    const double rate = __longlong_as_double((long long)c->rate_bits);
+    const long long cnt = (long long)c->ice_count;
+    const double tolc = c->eq_rel_tol * (double)c->pore_count;
     c->err_bits = 0ULL;
-    c->rate_bits = 0ULL;
+    c->ice_count = 0ULL;
+    c->pore_count = 0ULL;
     c->last_err = E;
-    if (c->eq_rate > 0.0 && rate <= c->eq_rate) {
-        c->equilibrium = 1;
-        c->t_eq = c->t;
-        c->accepted = 0;
-        c->done = 1;
-        return;
+    if (c->eq_window > 0.0) {
+        if (c->prev_count < 0 || fabs((double)(cnt - c->prev_count)) > tolc) {
+            c->prev_count = cnt;
+            c->last_change_t = c->t;
+        } else if (c->t - c->last_change_t >= c->eq_window) {
+            c->equilibrium = 1;
+            c->t_eq = c->t;
+            c->accepted = 0;
+            c->done = 1;
+            return;
+        }
     }
     const bool finite = E <= DBL_MAX;
     const bool accept = c->fixed || (finite && E <= c->tol);
@@ -358,6 +366,7 @@ static void fill_coefs(CoefT<T>& k, const pf_params& p, double h) {
     const double w = (p.alpha > 0 && p.xi > 0) ? 2.0 / (p.alpha * p.xi * p.xi) : 0.0;
     k.wa = T(w);
     k.wb = T(-p.zeta * w);
+    k.g_pore = T(p.zeta > 0 ? 0.5 / p.zeta : 1.0);
     k.klap = T(p.xi * p.xi * s);
     k.ksig = T(0.5 * p.xi * p.b * p.mu * p.alpha);
     k.kgrad = T(p.xi * p.xi * p.mu * p.alpha / (4.0 * h));
@@ -656,12 +665,14 @@ pf_status pf_set_state(pf_grid* g, const double* theta, const double* phi, doubl
     c->dt = dt;
     c->cur = 0;
     c->err_bits = 0;
-    c->rate_bits = 0;
+    c->ice_count = 0;
+    c->pore_count = 0;
+    c->prev_count = -1;
     c->done = 0;
     c->status = 0;
     c->last_err = 0;
     c->equilibrium = 0;
-    c->eq_rate = 0.0;
+    c->eq_window = 0.0;
     pf_status s = push_ctrl(g);
     if (s != PF_OK) return s;
     PF_CUDA(g, cudaStreamSynchronize(g->stream));
@@ -732,7 +743,7 @@ pf_status pf_rkm_step(pf_grid* g, double* dt_inout, double tol, int force_accept
     Ctrl* c = g->hctrl;
     c->dt_step = *dt_inout;
     c->dt = *dt_inout;
-    c->eq_rate = 0.0;
+    c->eq_window = 0.0;
     c->equilibrium = 0;
     c->land = 0;
     prepare_step(c);
@@ -811,7 +822,7 @@ pf_status pf_run_to(pf_grid* g, double t_end, double tol, long long max_steps, p
     c->t_end = t_end;
     c->tol = tol;
     c->fixed = 0;
-    c->eq_rate = 0.0;
+    c->eq_window = 0.0;
     c->equilibrium = 0;
     c->single = 0;
     c->max_attempts = max_steps;
@@ -836,7 +847,7 @@ pf_status pf_run_fixed(pf_grid* g, long long n_steps, double dt, pf_run_stats* s
     c->t_end = INFINITY;
     c->tol = 0.0;
     c->fixed = 1;
-    c->eq_rate = 0.0;
+    c->eq_window = 0.0;
     c->equilibrium = 0;
     c->single = 0;
     c->max_attempts = n_steps;
@@ -894,7 +905,7 @@ pf_status pf_profile_stages(pf_grid* g, int n_attempts, double* stage_ms) {
     c->fixed = 1;
     c->single = 1;
     c->dt_step = c->dt;
-    c->eq_rate = 0.0;
+    c->eq_window = 0.0;
     c->equilibrium = 0;
     c->land = 0;
     prepare_step(c);
@@ -1329,9 +1340,10 @@ pf_status pf_batch_autotune(pf_batch* b, const char* cache_path) {
     return batch_upload(b);
 }
 
-pf_status pf_batch_run_to(pf_batch* b, const double* t_end, const double* eq_rate, double tol, long long max_steps,
-                          pf_batch_result* res) {
+pf_status pf_batch_run_to(pf_batch* b, const double* t_end, const double* eq_window, double eq_rel_tol, double tol,
+                          long long max_steps, pf_batch_result* res) {
     if (!b) return bfail(nullptr, PF_E_INVALID, "batch is NULL");
+    if (!(eq_rel_tol >= 0.0)) return bfail(b, PF_E_INVALID, "eq_rel_tol must be >= 0");
     if (!t_end || !(tol > 0) || max_steps < 1) return bfail(b, PF_E_INVALID, "t_end, tol > 0, max_steps >= 1 required");
     if (max_steps > (1LL << 30)) max_steps = 1LL << 30;
     for (int q = 0; q < b->n; ++q) {
@@ -1346,8 +1358,11 @@ pf_status pf_batch_run_to(pf_batch* b, const double* t_end, const double* eq_rat
         c->n_acc = c->n_rej = 0;
         c->status = 0;
         c->err_bits = 0;
-        c->rate_bits = 0;
-        c->eq_rate = eq_rate ? eq_rate[q] : 0.0;
+        c->ice_count = 0;
+        c->pore_count = 0;
+        c->prev_count = -1;
+        c->eq_window = eq_window ? eq_window[q] : 0.0;
+        c->eq_rel_tol = eq_rel_tol;
         c->equilibrium = 0;
         c->t_eq = NAN;
         c->done = (c->t < t_end[q]) ? 0 : 1;

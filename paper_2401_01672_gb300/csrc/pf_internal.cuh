@@ -24,6 +24,7 @@ struct CoefT {
     T capL, dCG, dCI;
     T latent;
     T wa, wb;
+    T g_pore;    // 1/(2 zeta): cells with G below it have I_W > 1/2 (pore bulk, used by the equilibrium count)
     T klap;      // xi^2 / (2 h^2)
     T ksig;      // xi b mu alpha / 2                (SigmaP1-P)
     T kgrad;     // xi^2 mu alpha / (4 h)            (GradP, central differences)
@@ -61,8 +62,12 @@ struct Ctrl {
     float theta_bf;
     int pad1;
     unsigned long long err_bits;  // max of the error estimate over cells (bit pattern of a double >= 0)
-    unsigned long long rate_bits; // max |dphi/dt| of stage 1 (the current state), same encoding
-    double eq_rate;    // stop when max |dphi/dt| <= eq_rate (0 = never)
+    unsigned long long ice_count; // stage 1: #{phi > 1/2 and G < 1/(2 zeta)} of the current state (pore bulk)
+    unsigned long long pore_count; // stage 1: #{G < 1/(2 zeta)} (pore-bulk cells)
+    long long prev_count;         // ice count when it last changed by more than the tolerance (-1: none yet)
+    double eq_rel_tol;            // tolerated change of the ice count, relative to the pore-bulk cells
+    double last_change_t;         // time of that change
+    double eq_window;  // equilibrium: ice count unchanged for this long (0 = no test)
     double t_eq;       // time at which the equilibrium test held
     int equilibrium;   // the equilibrium test stopped the run
     int pad2;

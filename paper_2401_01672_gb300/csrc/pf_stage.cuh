@@ -52,6 +52,8 @@ __device__ __forceinline__ bool le_nonneg(double x, double y) { return __double_
 __device__ __forceinline__ bool le_nonneg(float x, float y) { return x <= y; }
 __device__ __forceinline__ bool ge_nonneg(double x, double y) { return __double_as_longlong(x) >= __double_as_longlong(y); }
 __device__ __forceinline__ bool ge_nonneg(float x, float y) { return x >= y; }
+__device__ __forceinline__ bool lt_nonneg(double x, double y) { return __double_as_longlong(x) < __double_as_longlong(y); }
+__device__ __forceinline__ bool lt_nonneg(float x, float y) { return x < y; }
 __device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }
 __device__ __forceinline__ bool positive(float x) { return x > 0.f; }
 
@@ -249,7 +251,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
     __syncthreads();
 
     unsigned long long ebits = 0ULL;  // max |E| as a bit pattern (NaN/Inf sort above every finite value)
-    unsigned long long rbits = 0ULL;  // stage 1: max |dphi/dt| as a bit pattern
+    unsigned int icount = 0, pcount = 0;  // stage 1: pore-bulk ice cells and pore-bulk cells of this thread
     int b = 0;
 
     for (int k = kb; k < ke; ++k) {
@@ -369,8 +371,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
                 if constexpr (HAS_PH) {
                     a.k1_ph[id] = dph;
                     a.ua_ph[id] = FMA(sc[0], dph, phc);
-                    const unsigned long long rb = abs_bits(dph);
-                    rbits = rb > rbits ? rb : rbits;
+                    // ice and cell counts of the pore bulk (I_W > 1/2) for the equilibrium test
+                    if (lt_nonneg(Gc, K.g_pore)) {
+                        ++pcount;
+                        if (!le_nonneg(phc, T(0.5))) ++icount;
+                    }
                 }
             } else if constexpr (STAGE == 2) {
                 if constexpr (F32) {
@@ -431,10 +436,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
         __syncthreads();
     }
 
-    if constexpr (STAGE == 5 || (STAGE == 1 && HAS_PH)) {
-        // block max of |E| (stage 5) or |dphi/dt| (stage 1) -> one atomicMax on the binary64 bit
-        // pattern (valid for values >= 0; NaN/Inf patterns sort above every finite value)
-        unsigned long long e = (STAGE == 5) ? ebits : rbits;
+    if constexpr (STAGE == 5) {
+        // block max of |E| -> one atomicMax on the binary64 bit pattern (valid for E >= 0; NaN/Inf
+        // patterns sort above every finite value)
+        unsigned long long e = ebits;
         if constexpr (F32) {
             const unsigned fb = (unsigned)e;
             e = (fb >= 0x7F800000u) ? 0x7FF0000000000000ULL
@@ -453,7 +458,27 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
                 const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
                 v = w > v ? w : v;
             }
-            if (tx == 0 && v > 0ULL) atomicMax(STAGE == 5 ? &ctrl->err_bits : &ctrl->rate_bits, v);
+            if (tx == 0 && v > 0ULL) atomicMax(&ctrl->err_bits, v);
+        }
+    }
+    if constexpr (STAGE == 1 && HAS_PH) {
+        // block sums of the two counts -> one atomicAdd each
+        unsigned int ci = icount, cp = pcount;
+        for (int o = 16; o > 0; o >>= 1) {
+            ci += __shfl_xor_sync(0xffffffffu, ci, o);
+            cp += __shfl_xor_sync(0xffffffffu, cp, o);
+        }
+        __shared__ unsigned int s_cnt[2][BY];
+        if (tx == 0) { s_cnt[0][ty] = ci; s_cnt[1][ty] = cp; }
+        __syncthreads();
+        if (ty == 0) {
+            unsigned int v = tx < BY ? s_cnt[0][tx] : 0u, w = tx < BY ? s_cnt[1][tx] : 0u;
+            for (int o = 16; o > 0; o >>= 1) {
+                v += __shfl_xor_sync(0xffffffffu, v, o);
+                w += __shfl_xor_sync(0xffffffffu, w, o);
+            }
+            if (tx == 0 && v > 0u) atomicAdd(&ctrl->ice_count, (unsigned long long)v);
+            if (tx == 0 && w > 0u) atomicAdd(&ctrl->pore_count, (unsigned long long)w);
         }
     }
     __syncthreads();  // the block may start another tile: shared memory is reused

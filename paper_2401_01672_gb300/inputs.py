@@ -131,7 +131,8 @@ def packing_rsa(shape, n_spheres, r_lo, r_hi, seed, max_tries=200000):
 def packing_boolean(shape, solid_fraction, radius_sampler, seed, max_spheres=10_000_000):
     """Overlap-allowed (Boolean) placement until the sharp voxel solid fraction reaches the target.
 
-    Centres are uniform over the box; spheres may cross the walls.
+    Centres are uniform over the box; spheres may cross the walls.  Spheres are added in groups sized
+    to a quarter of the remaining deficit (at least one), so small boxes do not overshoot.
     radius_sampler(g) draws one radius in voxels.
     Returns (spheres (n, 4) voxel units, achieved sharp solid fraction).
     """
@@ -141,19 +142,21 @@ def packing_boolean(shape, solid_fraction, radius_sampler, seed, max_spheres=10_
     total = mask.size
     out = []
     solid = 0
-    batch = 64
+    vol_sum, vol_n = 0.0, 0
     while solid < solid_fraction * total:
+        deficit = solid_fraction * total - solid
+        mean_vol = vol_sum / vol_n if vol_n else None
+        batch = 1 if mean_vol is None else int(max(1, min(64, 0.25 * deficit / mean_vol)))
         for _ in range(batch):
             r = float(radius_sampler(g))
             c = (g.uniform(0, n1), g.uniform(0, n2), g.uniform(0, n3))
             out.append((c[0], c[1], c[2], r))
             _stamp(mask, c, r)
+            vol_sum += 4.0 / 3.0 * math.pi * r ** 3
+            vol_n += 1
         solid = int(mask.sum())
         if len(out) > max_spheres:
             raise RuntimeError("Boolean packing did not reach the target")
-        # refine: finish one by one once close
-        if solid > 0.95 * solid_fraction * total:
-            batch = 1
     return np.array(out, dtype=np.float64), solid / total
 
 
@@ -305,7 +308,7 @@ class SweepInstance:
     phi0: np.ndarray
     dt0: float
     t_end: float
-    eq_rate: float            # max |dphi/dt| at equilibrium: 4 xi max|dphi/dt| <= 1e-3 mu dT
+    eq_window: float          # equilibrium: ice count unchanged for the time a free front (mu dT) crosses 20 cells
     sigma_scale: float
     dT: float
 
@@ -332,5 +335,27 @@ def sweep_instances(n=48, seed=20240108, h=1e-7, solid=0.60, sizes=None, seed_ra
         sp = sv.copy()
         sp *= h
         out.append(SweepInstance(shape, h, p, sp, phi0, 0.1 * p["alpha"] * h * h, 4 * N * h / (p["mu"] * dT),
-                                 1e-3 * p["mu"] * dT / (4 * h), sc, dT))
+                                 20 * h / (p["mu"] * dT), sc, dT))
+    return out
+
+
+def warmstart_instances(n, side=64, seed=20240109, h=1e-7, solid=0.5, dT_range=(0.5, 5.0), scale_range=(1.0, 10.0)):
+    """Micro-scale equilibria for the learned warm start: n cubes of `side`^3 cells, each with its own
+    Boolean bead packing (radii uniform in [10, 16] voxels, sharp solid fraction `solid`), supercooling
+    and surface-tension scale drawn log-uniformly, ice seeded on the bottom plane (nucleation at a
+    cooled face, as under the paper's cap), t_end = 4 L / (mu dT)."""
+    g = rng(seed)
+    out = []
+    for i in range(n):
+        shape = (side, side, side)
+        dT = float(math.exp(g.uniform(math.log(dT_range[0]), math.log(dT_range[1]))))
+        sc = float(math.exp(g.uniform(math.log(scale_range[0]), math.log(scale_range[1]))))
+        sv, _ = packing_boolean(shape, solid, uniform_radius(10.0, 16.0), seed + 7 + 13 * i)
+        phi0 = np.zeros((side, side, side))
+        phi0[0] = 1.0
+        p = default_params(xi=h, xi_G=0.4 * h, zeta=2.0, theta_micro=-dT, alpha=TABLE1["alpha"] / sc)
+        sp = sv.copy()
+        sp *= h
+        out.append(SweepInstance(shape, h, p, sp, phi0.ravel(), 0.1 * p["alpha"] * h * h,
+                                 4 * side * h / (p["mu"] * dT), 20 * h / (p["mu"] * dT), sc, dT))
     return out

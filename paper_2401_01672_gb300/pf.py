@@ -100,7 +100,7 @@ def load_library(path: str = LIB_PATH):
         "pf_batch_create": [i, C.POINTER(vp), C.POINTER(vp)],
         "pf_batch_destroy": [vp],
         "pf_batch_autotune": [vp, C.c_char_p],
-        "pf_batch_run_to": [vp, pd, pd, d, ll, C.POINTER(pf_batch_result)],
+        "pf_batch_run_to": [vp, pd, pd, d, d, ll, C.POINTER(pf_batch_result)],
         "pf_unfrozen_fraction_noalloc": [vp, vp, i, i, i, vp, vp, pd, pll, pll, pd],
     }
     for name, args in sig.items():
@@ -382,11 +382,11 @@ class Batch:
         self._check(_lib.pf_batch_autotune(self.handle, cache_path.encode() if cache_path else None))
         return [g.get_tiles() for g in self.grids]
 
-    def run_to(self, t_end, tol, max_steps, eq_rate=None):
+    def run_to(self, t_end, tol, max_steps, eq_window=None, eq_rel_tol=0.0):
         te = (C.c_double * self.n)(*[float(v) for v in t_end])
-        er = None if eq_rate is None else (C.c_double * self.n)(*[float(v) for v in eq_rate])
+        er = None if eq_window is None else (C.c_double * self.n)(*[float(v) for v in eq_window])
         res = (pf_batch_result * self.n)()
-        self._check(_lib.pf_batch_run_to(self.handle, te, er, float(tol), int(max_steps), res))
+        self._check(_lib.pf_batch_run_to(self.handle, te, er, float(eq_rel_tol), float(tol), int(max_steps), res))
         return [r.as_dict() for r in res]
 
     def iterations(self):
@@ -410,8 +410,8 @@ def pf_batch_create(grids):
     return Batch(grids)
 
 
-def pf_batch_run_to(b, t_end, tol, max_steps, eq_rate=None):
-    return b.run_to(t_end, tol, max_steps, eq_rate)
+def pf_batch_run_to(b, t_end, tol, max_steps, eq_window=None, eq_rel_tol=0.0):
+    return b.run_to(t_end, tol, max_steps, eq_window, eq_rel_tol)
 
 
 def pf_autotune(g, cache_path=None):
