@@ -43,7 +43,7 @@ SEED = 20240105
 N_SIDE = 256
 TOL = 1e-6
 
-# Algorithmic work per cell of each Merson stage kernel (full SigmaP1-P model); see the design doc.
+# Algorithmic work per cell of each Merson stage kernel (full SigmaP1-P model).
 # Bytes: stencil input fields + glass field + stage-combination operands read, outputs written,
 # each once per cell.  Binary64 path, bytes per cell for stages 1..5:
 BYTES_F64 = [56, 72, 88, 104, 104]          # sum 424 = 84.8 B per cell-stage
@@ -54,7 +54,7 @@ BYTES_F32 = [36, 28, 44, 44, 68]            # sum 220 = 44 B per cell-stage
 FLOPS_RHS = 64
 FLOPS_COMB = [4, 6, 8, 12, 24]
 # DRAM traffic per cell of the binary64 stage-5 kernel from one ncu capture at 192^3
-# (profiles/stage5_f64_full_sigmap1p_192.md): (632.0 + 101.8) MB / 7.08 M cells.  None once the
+# (dram__bytes_read.sum + dram__bytes_write.sum = 632.0 + 101.8 MB for 7.08 M cells).  None once the
 # kernel changes until it is captured again.
 TRAFFIC_F64_S5_PER_CELL = (632.0e6 + 101.8e6) / (192 ** 3)
 
@@ -403,7 +403,7 @@ def main():
     top_ms = prof[top]
     flops = (FLOPS_RHS + FLOPS_COMB[top]) * w.n_cells
     fp64_meas, fp32_meas, copy_meas = pf.pf_measure_peaks()
-    fp64_peak_tflops = 152 * 2 * 2 * 2.07e9 / 1e12   # 2 FP64 FMA / clk / SM
+    fp64_peak_tflops = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 binary64 FMA/clk x 2 flop x 2.07 GHz
     achieved_tf = flops / (top_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": f"merson_{stage_names[top]}_full_sigmap1p_f64",
                 "achieved": achieved_tf, "peak": fp64_peak_tflops, "unit": "TFLOP/s",

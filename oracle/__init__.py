@@ -24,6 +24,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pf_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle_pf.so")
+# tests/test_oracle_mutants.py points this at a library built from a deliberately broken copy
+_OVERRIDE = os.environ.get("PF_ORACLE_SO")
 _lib = None
 
 MODEL = {"full": 0, "temp": 1, "micro": 2}
@@ -32,6 +34,8 @@ REACTION = {"sigmap1p": 0, "gradp": 1}
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2 -ffp-contract=off, IEEE rounding as written)."""
+    if _OVERRIDE:
+        return _OVERRIDE
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
@@ -59,8 +63,7 @@ class ORModel(C.Structure):
 def _load():
     global _lib
     if _lib is None:
-        build()
-        lib = C.CDLL(_LIB)
+        lib = C.CDLL(build())
         P = C.POINTER
         d, i, ll = C.c_double, C.c_int, C.c_longlong
         pd, pll = P(d), P(ll)

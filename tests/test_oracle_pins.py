@@ -549,3 +549,43 @@ def test_uwc_brute_force(oracle_mod):
         assert r["n_water"] == int(w.sum()) and r["n_ice"] == int(ice.sum())
         assert abs(r["uwc"] - (1 - ice.sum() / w.sum())) < 1e-15
         assert abs(r["smooth"] - (1 - ((1 - g3) * p3).sum() / (1 - g3).sum())) < 1e-12
+
+
+def test_temp_phase_rate_is_chain_rule(oracle_mod):
+    """Sec. 2.3: dphi/dt = phi'(T) dT/dt with phi(T) of eq. (explicit-p-dependence-on-T); phi' is checked
+    against central finite differences of phi(T) itself."""
+    shape = (6, 5, 4)
+    for gamma in (2.0, 10.0):
+        o = mk(oracle_mod, shape, 1e-3, "temp", gamma=gamma, zeta=1.0)
+        th, _, G = I.random_fields(shape, 14, theta_scale=0.5)
+        dth, dph = o.rhs(G, th, None)
+        d = 1e-6
+        fd = (o.temp_phi(G, th + d) - o.temp_phi(G, th - d)) / (2 * d)
+        sel = np.abs(dth) > 1e-12 * np.max(np.abs(dth))
+        assert np.allclose(dph[sel] / dth[sel], fd[sel], rtol=1e-6, atol=1e-9 * np.max(np.abs(fd)))
+
+
+def test_steps_land_exactly_on_switch_times(oracle_mod):
+    """Steps are shortened to end exactly at t_freeze and t_end (eq. BC-temperature-cap switches there):
+    the step after the landing one starts at t_freeze exactly, for switching times that are not
+    representable sums of the step sizes."""
+    shape = (5, 4, 4)
+    h = 1e-3
+    for tf, te in ((1.0 / 3.0 * 10, 5.1), (2.718281828459045, 4.9), (1.4142135623730951, 3.3)):
+        o = mk(oracle_mod, shape, h, "full", dirichlet_faces=I.FACE_ZP, theta_freeze=-5.0, theta_thaw=2.0,
+               t_freeze=tf, alpha=4.17e6, xi=h)
+        r = o.run(np.zeros(o.N), np.full(o.N, 1.0), I.top_slab_indicator(shape, 1), 0.0, 0.07, te, 1e-5, 5000,
+                  trace=True)
+        acc = r["trace"][r["trace"][:, 3] == 1]
+        assert r["t"] == te
+        assert np.any(acc[:, 0] == tf)
+        assert np.all(acc[:, 1] > 1e-9)
+
+
+def test_long_step_lands_exactly(oracle_mod):
+    """A step shortened to reach t_freeze from t = 0.7 ends exactly at t_freeze even where
+    0.7 + (t_freeze - 0.7) rounds past it (t_freeze = 10/3 and e): the following step starts at t_freeze."""
+    for tf in (10.0 / 3.0, 2.718281828459045):
+        o = mk(oracle_mod, (1, 1, 1), 1e-6, "micro", xi=1e-6, alpha=1e9, t_freeze=tf)
+        r = o.run(np.zeros(1), None, np.array([0.3]), 0.7, 100.0, 50.0, 1.0, 2, fixed=True, trace=True)
+        assert r["trace"][1, 0] == tf
