@@ -54,9 +54,9 @@ BYTES_F32 = [36, 28, 44, 44, 68]            # sum 220 = 44 B per cell-stage
 FLOPS_RHS = 64
 FLOPS_COMB = [4, 6, 8, 12, 24]
 # DRAM traffic per cell of the binary64 stage-5 kernel from one ncu capture at 192^3
-# (dram__bytes_read.sum + dram__bytes_write.sum = 632.0 + 101.8 MB for 7.08 M cells).  None once the
-# kernel changes until it is captured again.
-TRAFFIC_F64_S5_PER_CELL = (632.0e6 + 101.8e6) / (192 ** 3)
+# (dram__bytes_read.sum + dram__bytes_write.sum per cell).  None once the kernel changes until it is
+# captured again.
+TRAFFIC_F64_S5_PER_CELL = None
 
 
 def env_int(k, d):

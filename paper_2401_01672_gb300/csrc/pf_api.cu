@@ -42,6 +42,7 @@ struct pf_grid {
     void* k4_th = nullptr; void* k4_ph = nullptr;
     double* G64 = nullptr;
     float* G32 = nullptr;
+    double* statics = nullptr;  // full model, binary64: 8 per-cell coefficient arrays (see StageArgs)
     double* scratch64 = nullptr;
     void* red = nullptr;
     size_t red_bytes = 0;
@@ -69,6 +70,9 @@ static pf_status fail(pf_grid* g, pf_status s, const std::string& msg) {
 }
 
 static bool is_f32(const pf_grid* g) { return g->prec == PF_PREC_FP32_FIELDS; }
+extern "C" {
+static pf_status refresh_g32(pf_grid* g);
+}
 static size_t fbytes(const pf_grid* g) { return is_f32(g) ? sizeof(float) : sizeof(double); }
 static bool has_th(const pf_grid* g) { return g->model != PF_MODEL_MICRO; }
 static bool has_ph(const pf_grid* g) { return g->model != PF_MODEL_TEMP; }
@@ -132,6 +136,26 @@ __global__ void k_glass_cap(double* G, int n1, int n2, int n3, double h, double 
         const double z = (k + 0.5) * h;
         const double g = 0.5 * (1.0 + tanh((z - x3cap) / (2.0 * xi_G)));
         if (g > G[q]) G[q] = g;
+    }
+}
+
+// Per-cell coefficients of the full model from G (eq. material-properties-blending-formula): with
+// w(phi) = A_w + B_w phi, A_w = w_L + G (w_G - w_L), B_w = (1 - G)(w_I - w_L):
+//   lambda' = A_lam + B_lam phi (scaled by 1/(2h^2)), W = 2 (1 - zeta G)/(alpha xi^2),
+//   rho c = A_rho A_c + (A_rho B_c + B_rho A_c) phi + B_rho B_c phi^2,  rho L = L A_rho + L B_rho phi.
+__global__ void k_full_statics(const double* __restrict__ G, double* __restrict__ S, long long n, CoefT<double> k) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const double g = G[q];
+        const double ar = fma(g, k.dRG, k.rhoL), br = fma(-g, k.dRI, k.dRI);
+        const double ac = fma(g, k.dCG, k.capL), bc = fma(-g, k.dCI, k.dCI);
+        S[q] = fma(g, k.dLG, k.lamL);
+        S[n + q] = fma(-g, k.dLI, k.dLI);
+        S[2 * n + q] = fma(k.wb, g, k.wa);
+        S[3 * n + q] = ar * ac;
+        S[4 * n + q] = fma(ar, bc, br * ac);
+        S[5 * n + q] = br * bc;
+        S[6 * n + q] = k.latent * ar;
+        S[7 * n + q] = k.latent * br;
     }
 }
 
@@ -367,6 +391,7 @@ static void fill_coefs(CoefT<T>& k, const pf_params& p, double h) {
     k.wa = T(w);
     k.wb = T(-p.zeta * w);
     k.g_pore = T(p.zeta > 0 ? 0.5 / p.zeta : 1.0);
+    k.wa_half = T(0.5 * w);
     k.klap = T(p.xi * p.xi * s);
     k.ksig = T(0.5 * p.xi * p.b * p.mu * p.alpha);
     k.kgrad = T(p.xi * p.xi * p.mu * p.alpha / (4.0 * h));
@@ -398,6 +423,8 @@ static StageArgs<T> make_args(pf_grid* g) {
     if constexpr (std::is_same<T, float>::value) a.G = g->G32;
     else a.G = g->G64;
     a.zc = g->zc;
+    a.statics = g->statics;
+    a.ncell = g->N;
     return a;
 }
 
@@ -536,6 +563,7 @@ pf_status pf_create_grid(int n1, int n2, int n3, double h, int model, int reacti
     }
     g->G64 = (double*)A(nd);
     if (is_f32(g)) g->G32 = (float*)A(sizeof(float) * g->N);
+    if (!is_f32(g) && model == PF_MODEL_FULL) g->statics = (double*)A(8 * nd);
     g->scratch64 = (double*)A(nd);
     g->red_bytes = sizeof(UwcPart) * (152 * 16 + 2);
     g->red = A(g->red_bytes);
@@ -570,6 +598,11 @@ pf_status pf_create_grid(int n1, int n2, int n3, double h, int model, int reacti
         destroy_impl(g);
         return fail(nullptr, PF_E_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
     }
+    if (refresh_g32(g) != PF_OK) {
+        cudaGetLastError();
+        destroy_impl(g);
+        return fail(nullptr, PF_E_CUDA, "initialisation of the glass-field coefficients failed");
+    }
     std::memset(g->hctrl, 0, sizeof(Ctrl));
     g->hctrl->dt = std::isfinite(p->dt_max) ? p->dt_max : 1e-3;
     g->hctrl->t_freeze = p->t_freeze;
@@ -586,7 +619,13 @@ pf_status pf_create_grid(int n1, int n2, int n3, double h, int model, int reacti
     return PF_OK;
 }
 
+// Derived copies of the glass field: binary32 copy (binary32 form), per-cell coefficients (full model, binary64).
 static pf_status refresh_g32(pf_grid* g) {
+    if (g->statics) {
+        k_full_statics<<<blocks_for(g->N, 256), 256, 0, g->stream>>>(g->G64, g->statics, g->N, g->k64);
+        count_launch();
+        PF_CUDA(g, cudaGetLastError());
+    }
     if (!g->G32) return PF_OK;
     k_to_f32<<<blocks_for(g->N, 256), 256, 0, g->stream>>>(g->G64, g->G32, g->N);
     count_launch();

@@ -25,6 +25,7 @@ struct CoefT {
     T latent;
     T wa, wb;
     T g_pore;    // 1/(2 zeta): cells with G below it have I_W > 1/2 (pore bulk, used by the equilibrium count)
+    T wa_half;   // wa / 2: the same test on W = 2 I_W / (alpha xi^2)
     T klap;      // xi^2 / (2 h^2)
     T ksig;      // xi b mu alpha / 2                (SigmaP1-P)
     T kgrad;     // xi^2 mu alpha / (4 h)            (GradP, central differences)
@@ -123,6 +124,11 @@ struct StageArgs {
     T* k3_th; T* k3_ph;
     T* k4_th; T* k4_ph;
     const T* G;              // glass field
+    // full model, binary64: per-cell coefficients precomputed from G (SoA, 8 arrays of n cells):
+    // [0] A_lam [1] B_lam (lambda' = A + B phi)  [2] W = 2 I_W/(alpha xi^2) before the max
+    // [3..5] C0, C1, C2 (rho c = C0 + phi (C1 + phi C2))  [6..7] D0, D1 (rho L = D0 + D1 phi)
+    const double* statics;
+    long long ncell;
     // plain right-hand side (stage 0)
     const T* in_th; const T* in_ph;
     T* out_th; T* out_ph;

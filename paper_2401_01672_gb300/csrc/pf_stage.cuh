@@ -119,6 +119,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
     constexpr bool HAS_PH = (MODEL != M_TEMP);   // phi integrated
     constexpr bool F32 = std::is_same<T, float>::value;
     constexpr bool TEMP = (MODEL == M_TEMP);
+    // full model in binary64: blends from precomputed per-cell coefficients (fewer binary64 operations)
+    constexpr bool STATIC = (!F32 && MODEL == M_FULL);
 
     Ctrl* ctrl = a.ctrl;
     int cur = 0;
@@ -190,22 +192,31 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
     __shared__ T s_ph[3][SY][SX];
     __shared__ T s_lam[HAS_TH ? 3 : 1][SY][SX];
 
-    // raw loads of one cell of plane kk (clamped: mirror ghosts)
-    auto fetch = [&](int kk, long long off, T& th, T& ph, T& G) {
+    const double* __restrict__ St = a.statics;
+    const long long NC = a.ncell;
+    // raw loads of one cell of plane kk (clamped: mirror ghosts); G holds A_lam and B B_lam when STATIC
+    auto fetch = [&](int kk, long long off, T& th, T& ph, T& G, T& B) {
         const long long id = (long long)min(max(kk, 0), n3 - 1) * plane + off;
-        G = Gf[id];
+        if constexpr (STATIC) {
+            G = T(St[id]);
+            B = T(St[NC + id]);
+        } else {
+            G = Gf[id];
+            B = T(0);
+        }
         if constexpr (HAS_TH) th = T(in_th[id]);
         else th = K.theta_micro;
         if constexpr (HAS_PH) ph = T(in_ph[id]);
         else ph = T(0);
     };
     // derived values: Temp phase field (eq. explicit-p-dependence-on-T) and blended conductivity
-    auto finish = [&](T th, T& ph, T G, T& lam, T& tg) {
+    auto finish = [&](T th, T& ph, T G, T B, T& lam, T& tg) {
         if constexpr (TEMP) {
             tg = dtanh(K.gamma * th);
             ph = T(0.5) * water_ind(G, K.zeta) * (T(1) - tg);
         }
-        if constexpr (HAS_TH) lam = blend3(G, ph, K.lamL, K.dLG, K.dLI);
+        if constexpr (STATIC) lam = FMA(ph, B, G);
+        else if constexpr (HAS_TH) lam = blend3(G, ph, K.lamL, K.dLG, K.dLI);
         else lam = T(0);
     };
     auto put = [&](int b, int y, int x, T th, T ph, T lam) {
@@ -229,22 +240,22 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
     T thc, phc, lamc, Gc, tgc = T(0);
     T thp, php, lamp, Gp, tgp = T(0);
     {
-        T Gm;
-        fetch(kb - 1, ooff, thm, phm, Gm);
-        finish(thm, phm, Gm, lamm, tgm);
-        fetch(kb, ooff, thc, phc, Gc);
-        finish(thc, phc, Gc, lamc, tgc);
+        T Gm, Bm, Bc, Bp;
+        fetch(kb - 1, ooff, thm, phm, Gm, Bm);
+        finish(thm, phm, Gm, Bm, lamm, tgm);
+        fetch(kb, ooff, thc, phc, Gc, Bc);
+        finish(thc, phc, Gc, Bc, lamc, tgc);
         put(0, ty + 1, tx + 1, thc, phc, lamc);
-        fetch(kb + 1, ooff, thp, php, Gp);
-        finish(thp, php, Gp, lamp, tgp);
+        fetch(kb + 1, ooff, thp, php, Gp, Bp);
+        finish(thp, php, Gp, Bp, lamp, tgp);
         put(1, ty + 1, tx + 1, thp, php, lamp);
         if (hal) {
-            T h_th, h_ph, h_G, h_lam, h_tg;
-            fetch(kb, hoff, h_th, h_ph, h_G);
-            finish(h_th, h_ph, h_G, h_lam, h_tg);
+            T h_th, h_ph, h_G, h_B, h_lam, h_tg;
+            fetch(kb, hoff, h_th, h_ph, h_G, h_B);
+            finish(h_th, h_ph, h_G, h_B, h_lam, h_tg);
             put(0, hy + 1, hx + 1, h_th, h_ph, h_lam);
-            fetch(kb + 1, hoff, h_th, h_ph, h_G);
-            finish(h_th, h_ph, h_G, h_lam, h_tg);
+            fetch(kb + 1, hoff, h_th, h_ph, h_G, h_B);
+            finish(h_th, h_ph, h_G, h_B, h_lam, h_tg);
             put(1, hy + 1, hx + 1, h_th, h_ph, h_lam);
         }
     }
@@ -256,15 +267,16 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
 
     for (int k = kb; k < ke; ++k) {
         // 1. raw values of plane k+2 (consumed after the arithmetic of plane k)
-        T rth, rph, rG, qth, qph, qG;
-        fetch(k + 2, ooff, rth, rph, rG);
-        if (hal) fetch(k + 2, hoff, qth, qph, qG);
+        T rth, rph, rG, rB, qth, qph, qG, qB;
+        fetch(k + 2, ooff, rth, rph, rG, rB);
+        if (hal) fetch(k + 2, hoff, qth, qph, qG, qB);
 
         const long long id = (long long)k * plane + (long long)j * n1 + i;
         // 2. stage-combination operands of this cell
         T y_t = T(0), y_p = T(0), k1t = T(0), k1p = T(0), k3t = T(0), k3p = T(0), k4t = T(0), k4p = T(0);
         double y_t64 = 0.0, y_p64 = 0.0;
         T ua_t = T(0), ua_p = T(0);
+        T sW = T(0), sC0 = T(0), sC1 = T(0), sC2 = T(0), sD0 = T(0), sD1 = T(0);
         if (inside) {
             if constexpr (STAGE >= 2) {
                 if constexpr (HAS_TH) k1t = a.k1_th[id];
@@ -285,6 +297,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
             if constexpr (F32 && STAGE == 3) {
                 if constexpr (HAS_TH) ua_t = a.ua_th[id];
                 if constexpr (HAS_PH) ua_p = a.ua_ph[id];
+            }
+            if constexpr (STATIC) {
+                sW = St[2 * NC + id];
+                sC0 = St[3 * NC + id]; sC1 = St[4 * NC + id]; sC2 = St[5 * NC + id];
+                sD0 = St[6 * NC + id]; sD1 = St[7 * NC + id];
             }
         }
 
@@ -324,7 +341,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
             // ---- Allen-Cahn rate (eq. Allen-Cahn-equation): dphi = W (klap lap + f/2), W = 2 I_W/(alpha xi^2)
             T dph = T(0);
             if constexpr (!TEMP) {
-                const T W = FMA(K.wb, Gc, K.wa);
+                T W;
+                if constexpr (STATIC) W = sW;
+                else W = FMA(K.wb, Gc, K.wa);
                 if (positive(W)) {
                     const T p_xm = s_ph[b][ty + 1][tx], p_xp = s_ph[b][ty + 1][tx + 2];
                     const T p_ym = s_ph[b][ty][tx + 1], p_yp = s_ph[b][ty + 2][tx + 1];
@@ -350,7 +369,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
             }
             // ---- latent-heat coupling
             T dth = T(0);
-            if constexpr (MODEL == M_FULL) {
+            if constexpr (STATIC) {
+                const T rhoc = FMA(phc, FMA(phc, sC2, sC1), sC0);
+                dth = FMA(FMA(phc, sD1, sD0), dph, div) * recip_pos(rhoc);
+            } else if constexpr (MODEL == M_FULL) {
                 const T rho = blend3(Gc, phc, K.rhoL, K.dRG, K.dRI);
                 const T cp = blend3(Gc, phc, K.capL, K.dCG, K.dCI);
                 dth = FMA(rho * K.latent, dph, div) * recip_pos(rho * cp);
@@ -372,7 +394,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
                     a.k1_ph[id] = dph;
                     a.ua_ph[id] = FMA(sc[0], dph, phc);
                     // ice and cell counts of the pore bulk (I_W > 1/2) for the equilibrium test
-                    if (lt_nonneg(Gc, K.g_pore)) {
+                    bool in_pore;
+                    if constexpr (STATIC) in_pore = ge_nonneg(sW, K.wa_half) && sW != K.wa_half;
+                    else in_pore = lt_nonneg(Gc, K.g_pore);
+                    if (in_pore) {
                         ++pcount;
                         if (!le_nonneg(phc, T(0.5))) ++icount;
                     }
@@ -402,16 +427,18 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
                     if constexpr (HAS_PH) { a.k4_ph[id] = dph; a.ub_ph[id] = FMA(sc[6], dph, FMA(-sc[5], k3p, FMA(sc[4], k1p, y_p))); }
                 }
             } else {  // STAGE 5
+                // |2k1 - 9k3 + 8k4 - k5| here; the factor dt/30 is applied to the block maximum
+                // (rounding is monotone, so max(dt/30 |x|) = dt/30 max |x| exactly)
                 if constexpr (HAS_TH) {
-                    const T inc = sc[1] * (k1t + FMA(T(4), k4t, dth));
-                    a.yo_th[cur ^ 1][id] = y_t64 + double(inc);
-                    const unsigned long long eb = abs_bits(sc[7] * FMA(T(2), k1t, FMA(T(-9), k3t, FMA(T(8), k4t, -dth))));
+                    if constexpr (F32) a.yo_th[cur ^ 1][id] = y_t64 + double(sc[1] * (k1t + FMA(T(4), k4t, dth)));
+                    else a.yo_th[cur ^ 1][id] = FMA(sc[1], k1t + FMA(T(4), k4t, dth), y_t64);
+                    const unsigned long long eb = abs_bits(FMA(T(2), k1t, FMA(T(-9), k3t, FMA(T(8), k4t, -dth))));
                     ebits = eb > ebits ? eb : ebits;
                 }
                 if constexpr (HAS_PH) {
-                    const T inc = sc[1] * (k1p + FMA(T(4), k4p, dph));
-                    a.yo_ph[cur ^ 1][id] = y_p64 + double(inc);
-                    const unsigned long long eb = abs_bits(sc[7] * FMA(T(2), k1p, FMA(T(-9), k3p, FMA(T(8), k4p, -dph))));
+                    if constexpr (F32) a.yo_ph[cur ^ 1][id] = y_p64 + double(sc[1] * (k1p + FMA(T(4), k4p, dph)));
+                    else a.yo_ph[cur ^ 1][id] = FMA(sc[1], k1p + FMA(T(4), k4p, dph), y_p64);
+                    const unsigned long long eb = abs_bits(FMA(T(2), k1p, FMA(T(-9), k3p, FMA(T(8), k4p, -dph))));
                     ebits = eb > ebits ? eb : ebits;
                 }
             }
@@ -421,7 +448,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
         const int b2 = (b + 2) % 3;
         {
             T lam2, tg2 = T(0);
-            finish(rth, rph, rG, lam2, tg2);
+            finish(rth, rph, rG, rB, lam2, tg2);
             put(b2, ty + 1, tx + 1, rth, rph, lam2);
             thm = thc; phm = phc; lamm = lamc; tgm = tgc;
             thc = thp; phc = php; lamc = lamp; Gc = Gp; tgc = tgp;
@@ -429,7 +456,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
         }
         if (hal) {
             T h_lam, h_tg;
-            finish(qth, qph, qG, h_lam, h_tg);
+            finish(qth, qph, qG, qB, h_lam, h_tg);
             put(b2, hy + 1, hx + 1, qth, qph, h_lam);
         }
         b = (b + 1) % 3;
@@ -458,7 +485,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
                 const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
                 v = w > v ? w : v;
             }
-            if (tx == 0 && v > 0ULL) atomicMax(&ctrl->err_bits, v);
+            if (tx == 0 && v > 0ULL) {
+                if (v < 0x7FF0000000000000ULL)  // finite: scale by dt/30 (binary64)
+                    v = (unsigned long long)__double_as_longlong(__longlong_as_double((long long)v) * ctrl->sc[7]);
+                atomicMax(&ctrl->err_bits, v);
+            }
         }
     }
     if constexpr (STAGE == 1 && HAS_PH) {

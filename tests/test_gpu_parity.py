@@ -333,3 +333,26 @@ def test_full_size_geometry_sampled(torch_cuda, orc):
     frac = np.mean(Gg >= 0.5)
     assert 0.5 < frac < 0.7
     g.close()
+
+
+@pytest.mark.parametrize("model", [I.MODEL_FULL, I.MODEL_TEMP])
+@pytest.mark.parametrize("harmonic,faces", [(1, I.FACE_ZP), (0, 63), (1, 63)])
+def test_rhs_parity_face_options(torch_cuda, orc, model, harmonic, faces):
+    """Harmonic-mean face conductivity and Dirichlet temperature on every face."""
+    torch = torch_cuda
+    shape = (35, 19, 41)
+    h = 2e-4
+    p = case_params(h, model, harmonic_mean=harmonic, dirichlet_faces=faces)
+    g, o = both(orc, shape, h, model, I.REACT_SIGMAP1P, p)
+    th, ph, G = I.random_fields(shape, 700 + harmonic + faces, theta_scale=3.0)
+    G[::13] = 1.0   # glass-only cells: lambda of both sides exercised
+    g.set_glass(G)
+    for t in (0.0, 20.0):
+        oth, oph = o.rhs(G, th, ph, t=t)
+        dth = torch.empty(g.N, device="cuda", dtype=torch.float64)
+        dph = torch.empty(g.N, device="cuda", dtype=torch.float64)
+        g.rhs(t, dev(torch, th), dev(torch, ph) if model != I.MODEL_TEMP else None, dth, dph)
+        torch.cuda.synchronize()
+        assert rel(dth.cpu().numpy(), oth) <= TOL
+        assert rel(dph.cpu().numpy(), oph) <= TOL
+    g.close()
