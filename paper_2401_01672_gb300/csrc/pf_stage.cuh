@@ -265,6 +265,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
     unsigned int icount = 0, pcount = 0;  // stage 1: pore-bulk ice cells and pore-bulk cells of this thread
     int b = 0;
 
+#pragma unroll 3
     for (int k = kb; k < ke; ++k) {
         // 1. raw values of plane k+2 (consumed after the arithmetic of plane k)
         T rth, rph, rG, rB, qth, qph, qG, qB;
