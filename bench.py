@@ -204,11 +204,20 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def time_form(torch, pf, w, precision, steps, warmup, stream):
+def set_tiles(g, tiles):
+    """Fixed tile shape, or the autotuner's choice (timed on the grid itself, state unchanged)."""
+    if tiles:
+        g.set_tiles(*tiles)
+    else:
+        g.autotune(None)
+
+
+def time_form(torch, pf, w, precision, steps, warmup, stream, tiles=None):
     """Device-timed adaptive attempts of one precision form; returns timing and stage profile."""
     g = pf.Grid(w.shape, w.h, w.model, w.reaction, precision, w.params, stream=stream)
     g.set_geometry(w.spheres, w.x3_cap)
     g.set_state(w.theta0, w.phi0, 0.0, 0.01)
+    set_tiles(g, tiles)
     # warm-up attempts (also reaches the steady step size of the initial transient)
     g.run_to(math.inf, TOL, warmup)
     torch.cuda.synchronize()
@@ -316,6 +325,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-form", action="store_true")
+    ap.add_argument("--tiles", type=int, nargs=2, metavar=("BY", "ZC"), default=None,
+                    help="fixed tile shape (block height, z chunk) instead of the autotuner's choice")
     ap.add_argument("--workload", default="full256", choices=["full256", "sweep48", "warmstart"],
                     help="full256: the binary64 bead workload (default); sweep48: the 48-instance micro-scale "
                          "sweep, batched binary32 persistent run vs the plain binary64 method")
@@ -369,6 +380,8 @@ def main():
     g = pf.Grid(w.shape, w.h, w.model, w.reaction, I.PREC_FP64, w.params, stream=stream)
     g.set_geometry(w.spheres, w.x3_cap)
     g.set_state(w.theta0, w.phi0, 0.0, 0.01)
+    set_tiles(g, args.tiles)
+    tiles = g.get_tiles()
     g.run_to(math.inf, TOL, args.warmup)
     barrier()
     l0 = pf.pf_kernel_launches()
@@ -440,13 +453,13 @@ def main():
     # ---------------- binary32-field form on the same workload
     forms = {}
     if not args.no_fp32_form:
-        g32, s32, ms32, l32, prof32 = time_form(torch, pf, w, I.PREC_FP32, args.steps, args.warmup, stream)
+        g32, s32, ms32, l32, prof32 = time_form(torch, pf, w, I.PREC_FP32, args.steps, args.warmup, stream, args.tiles)
         att32 = s32["n_accepted"] + s32["n_rejected"]
         top32 = int(np.argmax(prof32[:5]))
         gbs32 = BYTES_F32[top32] * w.n_cells / (prof32[top32] * 1e-3) / 1e9
         forms["fp32_fields"] = {
             "value": w.n_cells * 5 * att32 / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32 / max(att32, 1),
-            "gpu_launches": l32, "dtype": "f32 fields / f64 state",
+            "gpu_launches": l32, "dtype": "f32 fields / f64 state", "tiles_by_zc": list(g32.get_tiles()),
             "roofline": {"bound": "hbm", "kernel": f"merson_{stage_names[top32]}_full_sigmap1p_f32",
                          "achieved": gbs32, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": gbs32 / peaks["hbm_gbs"],
@@ -468,6 +481,7 @@ def main():
                            "solid_fraction": round(w.extra["solid_fraction_sharp"], 4), "tol": TOL,
                            "attempts": attempts, "accepted": s["n_accepted"],
                            "l2": "inputs larger than L2 (about 2 GB working set)",
+                           "tiles_by_zc": list(tiles),
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk.summary(), "forms": forms, "wall_s_timed": t_wall}

@@ -1057,15 +1057,22 @@ static const int kTuneZC[5] = {4, 8, 16, 32, 64};
 
 // Time the plain right-hand side (the stage kernels' common body) for every (by, zc) candidate on the
 // grid itself; ms[b][z] = best of 3 launches (infinity for skipped candidates).
+// Device time of one Merson attempt's five stage kernels for every tile shape (best of three after
+// a warm-up).  The controller is not launched: the state, the time and the step counters stay as
+// they are (stage 5 writes only the spare state buffer), and the control block is restored after.
 static pf_status tune_table(pf_grid* g, double ms[3][5]) {
     pf_status s = sync_ctrl_to_host(g);
     if (s != PF_OK) return s;
-    const int cur = g->hctrl->cur;
-    const int nb = blocks_for(g->N, 256);
-    if (is_f32(g)) {
-        if (has_th(g)) { k_to_f32<<<nb, 256, 0, g->stream>>>(g->y_th[cur], (float*)g->ua_th, g->N); count_launch(); }
-        if (has_ph(g)) { k_to_f32<<<nb, 256, 0, g->stream>>>(g->y_ph[cur], (float*)g->ua_ph, g->N); count_launch(); }
-    }
+    const Ctrl saved = *g->hctrl;
+    Ctrl* c = g->hctrl;
+    c->dt_step = c->dt;
+    prepare_step(c);
+    c->done = 0;
+    c->status = 0;
+    c->fixed = 1;
+    c->single = 1;
+    s = push_ctrl(g);
+    if (s != PF_OK) return s;
     cudaEvent_t e0, e1;
     PF_CUDA(g, cudaEventCreate(&e0));
     PF_CUDA(g, cudaEventCreate(&e1));
@@ -1081,17 +1088,7 @@ static pf_status tune_table(pf_grid* g, double ms[3][5]) {
             double best = INFINITY;
             for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
                 e = cudaEventRecord(e0, g->stream);
-                if (is_f32(g)) {
-                    StageArgs<float> a = make_args<float>(g);
-                    a.in_th = (const float*)g->ua_th; a.in_ph = (const float*)g->ua_ph;
-                    a.out_th = (float*)g->ub_th; a.out_ph = (float*)g->ub_ph;
-                    if (e == cudaSuccess) e = launch_stage_f32(g->model, g->rx, 0, a, g->by, g->stream);
-                } else {
-                    StageArgs<double> a = make_args<double>(g);
-                    a.in_th = g->y_th[cur]; a.in_ph = g->y_ph[cur];
-                    a.out_th = (double*)g->ub_th; a.out_ph = (double*)g->ub_ph;
-                    if (e == cudaSuccess) e = launch_stage_f64(g->model, g->rx, 0, a, g->by, g->stream);
-                }
+                for (int st = 1; st <= 5 && e == cudaSuccess; ++st) e = launch_stage(g, st, g->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(e1, g->stream);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 float t = 0.f;
@@ -1105,6 +1102,10 @@ static pf_status tune_table(pf_grid* g, double ms[3][5]) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return fail(g, PF_E_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    *g->hctrl = saved;
+    s = push_ctrl(g);
+    if (s != PF_OK) return s;
+    PF_CUDA(g, cudaStreamSynchronize(g->stream));
     return PF_OK;
 }
 

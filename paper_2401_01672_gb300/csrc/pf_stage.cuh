@@ -16,10 +16,11 @@
 // lambda is evaluated once per plane visit; the z neighbours of a thread's own
 // column stay in registers.  The raw values of plane k+2 are loaded while plane
 // k is computed (three-plane shared-memory ring, one barrier per plane), and the
-// stage-combination operands are loaded before the right-hand-side arithmetic,
-// so memory latency overlaps computation.  Cells outside the grid are replaced by
-// the nearest boundary cell (mirror ghost), which makes the interior formula give
-// zero flux on every face; Dirichlet faces add their half-cell flux separately.
+// stage-combination operands are loaded before the right-hand-side arithmetic
+// (binary32 stages 2-4: one plane ahead), so memory latency overlaps computation.
+// Cells outside the grid are replaced by the nearest boundary cell (mirror ghost),
+// which makes the interior formula give zero flux on every face; Dirichlet faces
+// add their half-cell flux separately.
 //
 // Binary64 operation count: the binary64 pipe of sm_103a issues two FMAs per clock
 // per SM, a sixtieth of the binary32 rate, so the binary64 kernels keep every
@@ -76,6 +77,44 @@ __device__ __forceinline__ double recip_pos(double x) {
     return r;
 }
 __device__ __forceinline__ float recip_pos(float x) { return __frcp_rn(x); }
+
+// Conversions between binary64 and binary32 in 32-bit integer instructions on the two halves of the
+// binary64 bit pattern.  The binary64 pipe of sm_103a (two operations per clock per SM) executes the
+// conversion instructions and 64-bit integer arithmetic too, which would make them a large part of
+// the binary32 kernels that touch the binary64 state (stages 1 and 5).  Both follow the IEEE 754
+// formats: the exponent is rebiased by 1023 - 127 = 896 and the significand is shifted by
+// 52 - 23 = 29 bits.  Values outside the range of binary32 normal numbers (except zero) take the
+// conversion instruction.
+
+// binary32 -> binary64 (exact)
+__device__ __forceinline__ double widen(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned a = b & 0x7FFFFFFFu;
+    if (a - 0x00800000u < 0x7F000000u)  // exponent field in [1, 254]: normal
+        return __hiloint2double((int)(((a >> 3) + (896u << 20)) | (b & 0x80000000u)), (int)(a << 29));
+    if (a == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+    return (double)x;
+}
+
+// binary64 -> binary32, round to nearest, ties to even: the 29 dropped significand bits (the low 29
+// bits of the low word) are rounded by adding 2^28 - 1 plus the lowest kept bit; a carry out of the
+// significand increments the exponent (up to infinity, as rounding to nearest requires).  The shift
+// of the high word drops the top exponent bits; the rebias is exact modulo 2^32.
+__device__ __forceinline__ float narrow(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned a = hi & 0x7FFFFFFFu;
+    if ((a >> 20) - 897u < 254u) {  // exponent field in [897, 1150]: binary32 normal
+        unsigned f = ((a << 3) | (lo >> 29)) - (896u << 23);
+        f += ((lo & 0x1FFFFFFFu) + 0x0FFFFFFFu + (f & 1u)) >> 29;
+        return __uint_as_float(f | (hi & 0x80000000u));
+    }
+    if ((a | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
+    return (float)x;
+}
+
+template <typename T> __device__ __forceinline__ T to_T(double x) { return T(x); }
+template <> __device__ __forceinline__ float to_T<float>(double x) { return narrow(x); }
+template <typename T> __device__ __forceinline__ T to_T(float x) { return T(x); }
 
 // eq. (Sigma-limiter)
 template <typename T>
@@ -195,7 +234,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
     const double* __restrict__ St = a.statics;
     const long long NC = a.ncell;
     // raw loads of one cell of plane kk (clamped: mirror ghosts); G holds A_lam and B B_lam when STATIC
-    auto fetch = [&](int kk, long long off, T& th, T& ph, T& G, T& B) {
+    // (theta and phi stay in the input type until `cvt`, so that a conversion does not wait for its
+    // load where the load is issued)
+    auto fetch = [&](int kk, long long off, TIN& th, TIN& ph, T& G, T& B) {
         const long long id = (long long)min(max(kk, 0), n3 - 1) * plane + off;
         if constexpr (STATIC) {
             G = T(St[id]);
@@ -204,10 +245,21 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
             G = Gf[id];
             B = T(0);
         }
-        if constexpr (HAS_TH) th = T(in_th[id]);
+        if constexpr (HAS_TH) th = in_th[id];
+        else th = TIN(0);
+        if constexpr (HAS_PH) ph = in_ph[id];
+        else ph = TIN(0);
+    };
+    auto cvt = [&](TIN rth, TIN rph, T& th, T& ph) {
+        if constexpr (HAS_TH) th = to_T<T>(rth);
         else th = K.theta_micro;
-        if constexpr (HAS_PH) ph = T(in_ph[id]);
+        if constexpr (HAS_PH) ph = to_T<T>(rph);
         else ph = T(0);
+    };
+    auto fetch_cvt = [&](int kk, long long off, T& th, T& ph, T& G, T& B) {
+        TIN rth, rph;
+        fetch(kk, off, rth, rph, G, B);
+        cvt(rth, rph, th, ph);
     };
     // derived values: Temp phase field (eq. explicit-p-dependence-on-T) and blended conductivity
     auto finish = [&](T th, T& ph, T G, T B, T& lam, T& tg) {
@@ -235,26 +287,48 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
         nd_xy += ((dmask & 4) && j == 0) + ((dmask & 8) && j == n2 - 1);
     }
 
+    // Binary32 stages 2-4 move few bytes and do little arithmetic per cell, so memory latency
+    // bounds them: their stage-combination operands are loaded one plane ahead.  (Binary64 kernels
+    // are bound by the binary64 pipe, and binary32 stage 5 by its register budget: both load
+    // their operands within the plane.)
+    constexpr bool PF = F32 && STAGE >= 2 && STAGE <= 4;
+    T n_k1t = T(0), n_k1p = T(0), n_k3t = T(0), n_k3p = T(0), n_uat = T(0), n_uap = T(0);
+    if constexpr (PF) {
+        if (inside && kb < ke) {
+            const long long q = (long long)kb * plane + (long long)j * n1 + i;
+            if constexpr (HAS_TH) n_k1t = a.k1_th[q];
+            if constexpr (HAS_PH) n_k1p = a.k1_ph[q];
+            if constexpr (STAGE == 3) {
+                if constexpr (HAS_TH) n_uat = a.ua_th[q];
+                if constexpr (HAS_PH) n_uap = a.ua_ph[q];
+            }
+            if constexpr (STAGE == 4) {
+                if constexpr (HAS_TH) n_k3t = a.k3_th[q];
+                if constexpr (HAS_PH) n_k3p = a.k3_ph[q];
+            }
+        }
+    }
+
     // ---- prologue: own column at kb-1, kb, kb+1; planes kb, kb+1 into the ring
     T thm, phm, lamm, tgm = T(0);
     T thc, phc, lamc, Gc, tgc = T(0);
     T thp, php, lamp, Gp, tgp = T(0);
     {
         T Gm, Bm, Bc, Bp;
-        fetch(kb - 1, ooff, thm, phm, Gm, Bm);
+        fetch_cvt(kb - 1, ooff, thm, phm, Gm, Bm);
         finish(thm, phm, Gm, Bm, lamm, tgm);
-        fetch(kb, ooff, thc, phc, Gc, Bc);
+        fetch_cvt(kb, ooff, thc, phc, Gc, Bc);
         finish(thc, phc, Gc, Bc, lamc, tgc);
         put(0, ty + 1, tx + 1, thc, phc, lamc);
-        fetch(kb + 1, ooff, thp, php, Gp, Bp);
+        fetch_cvt(kb + 1, ooff, thp, php, Gp, Bp);
         finish(thp, php, Gp, Bp, lamp, tgp);
         put(1, ty + 1, tx + 1, thp, php, lamp);
         if (hal) {
             T h_th, h_ph, h_G, h_B, h_lam, h_tg;
-            fetch(kb, hoff, h_th, h_ph, h_G, h_B);
+            fetch_cvt(kb, hoff, h_th, h_ph, h_G, h_B);
             finish(h_th, h_ph, h_G, h_B, h_lam, h_tg);
             put(0, hy + 1, hx + 1, h_th, h_ph, h_lam);
-            fetch(kb + 1, hoff, h_th, h_ph, h_G, h_B);
+            fetch_cvt(kb + 1, hoff, h_th, h_ph, h_G, h_B);
             finish(h_th, h_ph, h_G, h_B, h_lam, h_tg);
             put(1, hy + 1, hx + 1, h_th, h_ph, h_lam);
         }
@@ -268,7 +342,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
 #pragma unroll 3
     for (int k = kb; k < ke; ++k) {
         // 1. raw values of plane k+2 (consumed after the arithmetic of plane k)
-        T rth, rph, rG, rB, qth, qph, qG, qB;
+        TIN rth, rph, qth, qph;
+        T rG, rB, qG, qB;
         fetch(k + 2, ooff, rth, rph, rG, rB);
         if (hal) fetch(k + 2, hoff, qth, qph, qG, qB);
 
@@ -278,7 +353,23 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
         double y_t64 = 0.0, y_p64 = 0.0;
         T ua_t = T(0), ua_p = T(0);
         T sW = T(0), sC0 = T(0), sC1 = T(0), sC2 = T(0), sD0 = T(0), sD1 = T(0);
-        if (inside) {
+        if constexpr (PF) {
+            // take the operands loaded during the previous plane, then load those of plane k+1
+            k1t = n_k1t; k1p = n_k1p; k3t = n_k3t; k3p = n_k3p; ua_t = n_uat; ua_p = n_uap;
+            if (inside && k + 1 < ke) {
+                const long long q = id + plane;
+                if constexpr (HAS_TH) n_k1t = a.k1_th[q];
+                if constexpr (HAS_PH) n_k1p = a.k1_ph[q];
+                if constexpr (STAGE == 3) {
+                    if constexpr (HAS_TH) n_uat = a.ua_th[q];
+                    if constexpr (HAS_PH) n_uap = a.ua_ph[q];
+                }
+                if constexpr (STAGE == 4) {
+                    if constexpr (HAS_TH) n_k3t = a.k3_th[q];
+                    if constexpr (HAS_PH) n_k3p = a.k3_ph[q];
+                }
+            }
+        } else if (inside) {
             if constexpr (STAGE >= 2) {
                 if constexpr (HAS_TH) k1t = a.k1_th[id];
                 if constexpr (HAS_PH) k1p = a.k1_ph[id];
@@ -431,13 +522,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
                 // |2k1 - 9k3 + 8k4 - k5| here; the factor dt/30 is applied to the block maximum
                 // (rounding is monotone, so max(dt/30 |x|) = dt/30 max |x| exactly)
                 if constexpr (HAS_TH) {
-                    if constexpr (F32) a.yo_th[cur ^ 1][id] = y_t64 + double(sc[1] * (k1t + FMA(T(4), k4t, dth)));
+                    if constexpr (F32) a.yo_th[cur ^ 1][id] = y_t64 + widen(sc[1] * (k1t + FMA(T(4), k4t, dth)));
                     else a.yo_th[cur ^ 1][id] = FMA(sc[1], k1t + FMA(T(4), k4t, dth), y_t64);
                     const unsigned long long eb = abs_bits(FMA(T(2), k1t, FMA(T(-9), k3t, FMA(T(8), k4t, -dth))));
                     ebits = eb > ebits ? eb : ebits;
                 }
                 if constexpr (HAS_PH) {
-                    if constexpr (F32) a.yo_ph[cur ^ 1][id] = y_p64 + double(sc[1] * (k1p + FMA(T(4), k4p, dph)));
+                    if constexpr (F32) a.yo_ph[cur ^ 1][id] = y_p64 + widen(sc[1] * (k1p + FMA(T(4), k4p, dph)));
                     else a.yo_ph[cur ^ 1][id] = FMA(sc[1], k1p + FMA(T(4), k4p, dph), y_p64);
                     const unsigned long long eb = abs_bits(FMA(T(2), k1p, FMA(T(-9), k3p, FMA(T(8), k4p, -dph))));
                     ebits = eb > ebits ? eb : ebits;
@@ -448,17 +539,19 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
         // 3. finish plane k+2 into the ring slot of plane k-1; rotate the own column
         const int b2 = (b + 2) % 3;
         {
-            T lam2, tg2 = T(0);
-            finish(rth, rph, rG, rB, lam2, tg2);
-            put(b2, ty + 1, tx + 1, rth, rph, lam2);
+            T cth, cph, lam2, tg2 = T(0);
+            cvt(rth, rph, cth, cph);
+            finish(cth, cph, rG, rB, lam2, tg2);
+            put(b2, ty + 1, tx + 1, cth, cph, lam2);
             thm = thc; phm = phc; lamm = lamc; tgm = tgc;
             thc = thp; phc = php; lamc = lamp; Gc = Gp; tgc = tgp;
-            thp = rth; php = rph; lamp = lam2; Gp = rG; tgp = tg2;
+            thp = cth; php = cph; lamp = lam2; Gp = rG; tgp = tg2;
         }
         if (hal) {
-            T h_lam, h_tg;
-            finish(qth, qph, qG, qB, h_lam, h_tg);
-            put(b2, hy + 1, hx + 1, qth, qph, h_lam);
+            T h_th, h_ph, h_lam, h_tg;
+            cvt(qth, qph, h_th, h_ph);
+            finish(h_th, h_ph, qG, qB, h_lam, h_tg);
+            put(b2, hy + 1, hx + 1, h_th, h_ph, h_lam);
         }
         b = (b + 1) % 3;
         __syncthreads();
