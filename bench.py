@@ -54,9 +54,12 @@ BYTES_F32 = [36, 28, 44, 44, 68]            # sum 220 = 44 B per cell-stage
 FLOPS_RHS = 64
 FLOPS_COMB = [4, 6, 8, 12, 24]
 # DRAM traffic per cell of the binary64 stage-5 kernel from one ncu capture at 192^3
-# (dram__bytes_read.sum + dram__bytes_write.sum per cell).  None once the kernel changes until it is
-# captured again.
-TRAFFIC_F64_S5_PER_CELL = None
+# (dram__bytes_read.sum + dram__bytes_write.sum = 1144.4 MB over 7,077,888 cells).  None once the
+# kernel changes until it is captured again.  The kernel itself is written to move 160 B/cell: the
+# method's 104 B plus 56 B of precomputed per-cell blend coefficients, read instead of recomputed on
+# the binary64 pipe that bounds it.
+TRAFFIC_F64_S5_PER_CELL = 161.7
+KERNEL_BYTES_F64_S5 = 160
 
 
 def env_int(k, d):
@@ -425,6 +428,7 @@ def main():
                 "peak_measured_fp64_tflops": fp64_meas, "frac_of_measured": achieved_tf / fp64_meas,
                 "measured_fp32_tflops": fp32_meas, "measured_copy_gbs": copy_meas,
                 "algorithmic_per_launch": {"flops": flops, "bytes": BYTES_F64[top] * w.n_cells},
+                "kernel_bytes_per_launch": (KERNEL_BYTES_F64_S5 * w.n_cells if top == 4 else None),
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (binary64 pipe)",
                 "hbm_achieved_gbs": BYTES_F64[top] * w.n_cells / (top_ms * 1e-3) / 1e9,
                 "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peak_kind,

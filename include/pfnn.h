@@ -10,8 +10,9 @@
  *     slice [off, off + C) of a buffer with ld channels per voxel.  FP32 gradient buffers use the
  *     same layout.
  *   - Convolutions: 3x3x3 taps, zero padding 1, stride 1.  Weights [27][Cout][Cin] bfloat16, tap
- *     t = (dz+1)*9 + (dy+1)*3 + (dx+1).  Products on the tensor cores (mma.sync m16n8k16, bf16 in,
- *     fp32 accumulation).
+ *     t = (dz+1)*9 + (dy+1)*3 + (dx+1).  Forward and backward-data products on the fifth-generation
+ *     tensor cores (TMA-staged operands, tcgen05.mma with fp32 accumulators in tensor memory);
+ *     weight gradients with mma.sync m16n8k16 (bf16 in, fp32 accumulation).
  *   - All pointers are DEVICE pointers borrowed for the call (caller-owned, e.g. torch tensors);
  *     16-byte alignment of every bf16 row is required (ld, off multiples of 8).  Work is enqueued on
  *     `stream` (cudaStream_t, NULL = legacy default stream); nothing synchronises.
@@ -28,11 +29,17 @@ extern "C" {
 /* Forward (flip = 0): y[v][co] = act(bias[co] + sum_{t,ci} x[v + off(t)][ci] w[t][co][ci]).
  * Backward data (flip = 1, w = transposed weights [27][Cin][Cout], cin/cout swapped):
  *   dx[v][ci] = sum_{t,co} dy[v - off(t)][co] w[t][co][ci].
- * cin a multiple of 16; cout in {8, 16, 32} or any multiple of 8 >= 64; act = ReLU when relu != 0.
- * Output either bf16 (y_bf16) or fp32 (y_f32; accumulate != 0 adds to it). */
+ * cin a multiple of 16; cout a multiple of 16 up to 256; act = ReLU when relu != 0.  ldx, xoff, ldy and
+ * yoff multiples of 8, x, w and the output 16-byte aligned.  Output either bf16 (y_bf16) or fp32 (y_f32;
+ * accumulate != 0 adds to it).  A kernel whose pipeline wait gives up (bounded; it does not happen in
+ * normal operation) finishes without storing and raises the flag that pfnn_status reports. */
 pf_status pfnn_conv3d(const void* x, int ldx, int xoff, const void* w, int cin, int cout, const float* bias, int relu,
                       int flip, void* y_bf16, float* y_f32, int ldy, int yoff, int accumulate, int n, int d, int h,
                       int wd, void* stream);
+
+/* Reads and clears the device flag of the tensor-core convolutions (1 = a pipeline wait gave up since
+ * the last call, so some output was not written).  Synchronous: waits for the device. */
+pf_status pfnn_status(int* failed);
 
 /* Weight gradient: dw[t][co][ci] += sum_v dy[v][co] x[v + off(t)][ci]  (fp32 atomics, split over voxels). */
 pf_status pfnn_conv3d_wgrad(const void* dy, int lddy, int dyoff, int cout, const void* x, int ldx, int xoff, int cin,

@@ -1,6 +1,7 @@
 // Kernels of the learned warm start: a 3D convolutional encoder-decoder trained and run with BF16
-// activations and weights, FP32 accumulation on the tensor cores (mma.sync m16n8k16), FP32 master
-// weights and gradients.
+// activations and weights, FP32 accumulation, FP32 master weights and gradients.  The forward and
+// backward-data convolutions run on tcgen05 (pfnn_umma.cu); this file holds the weight gradient
+// (mma.sync m16n8k16) and the data-movement, head and optimiser kernels.
 //
 // Layout: activations N x D x H x W x C (channels last), bf16; a tensor may be a channel slice
 // [off, off + C) of a wider buffer with ld channels per voxel (skip concatenation is free).
@@ -25,11 +26,6 @@ constexpr int KC = 16;     // k chunk = one mma k step
 constexpr int KP = 24;     // padded smem row length (bf16): conflict-free fragment loads
 constexpr int NTHR = 128;  // 4 warps, 16 rows each
 
-struct Dims {
-    int n, d, h, w;
-    long long vox() const { return (long long)n * d * h * w; }
-};
-
 __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -46,89 +42,6 @@ __device__ __forceinline__ void vox_coord(long long v, int D, int H, int W, int&
     r /= H;
     z = (int)(r % D);
     b = (int)(r / D);
-}
-
-// Forward / backward-data implicit GEMM.  BN = output channels per block (16, 32 or 64).
-// flip = 0: input voxel = v + off(t); flip = 1: v - off(t).
-template <int BN>
-__global__ void __launch_bounds__(NTHR)
-k_conv_gemm(const __nv_bfloat16* __restrict__ x, int ldx, int xoff, const __nv_bfloat16* __restrict__ w, int cin,
-            int cout, const float* __restrict__ bias, int relu, int flip, __nv_bfloat16* __restrict__ y,
-            float* __restrict__ yf, int ldy, int yoff, int accumulate, int D, int H, int W, long long nvox) {
-    __shared__ __align__(16) __nv_bfloat16 As[BM][KP];
-    __shared__ __align__(16) __nv_bfloat16 Bs[BN][KP];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = lane >> 2, t4 = lane & 3;
-    const long long v0 = (long long)blockIdx.x * BM;
-    const int co0 = blockIdx.y * BN;
-
-    // this thread's A-load row (voxel) and half (8 channels)
-    const int arow = tid >> 1, ahalf = tid & 1;
-    const long long av = v0 + arow;
-    int ab = 0, az = 0, ay = 0, ax = 0;
-    const bool avalid = av < nvox;
-    if (avalid) vox_coord(av, D, H, W, ab, az, ay, ax);
-
-    float acc[BN / 8][4];
-#pragma unroll
-    for (int j = 0; j < BN / 8; ++j)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
-
-    for (int tap = 0; tap < 27; ++tap) {
-        int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-        if (flip) { dz = -dz; dy = -dy; dx = -dx; }
-        const int sz = az + dz, sy = ay + dy, sx = ax + dx;
-        const bool inb = avalid && sz >= 0 && sz < D && sy >= 0 && sy < H && sx >= 0 && sx < W;
-        const long long sv = (((long long)ab * D + sz) * H + sy) * W + sx;
-        for (int c0 = 0; c0 < cin; c0 += KC) {
-            uint4 va = make_uint4(0, 0, 0, 0);
-            if (inb) va = *reinterpret_cast<const uint4*>(x + sv * ldx + xoff + c0 + ahalf * 8);
-            *reinterpret_cast<uint4*>(&As[arow][ahalf * 8]) = va;
-            for (int r = tid; r < BN * 2; r += NTHR) {
-                const int brow = r >> 1, bhalf = r & 1;
-                uint4 vb = make_uint4(0, 0, 0, 0);
-                if (co0 + brow < cout)
-                    vb = *reinterpret_cast<const uint4*>(w + ((long long)tap * cout + co0 + brow) * cin + c0 + bhalf * 8);
-                *reinterpret_cast<uint4*>(&Bs[brow][bhalf * 8]) = vb;
-            }
-            __syncthreads();
-            uint32_t a[4];
-            const int r0 = warp * 16 + g;
-            a[0] = *reinterpret_cast<const uint32_t*>(&As[r0][2 * t4]);
-            a[1] = *reinterpret_cast<const uint32_t*>(&As[r0 + 8][2 * t4]);
-            a[2] = *reinterpret_cast<const uint32_t*>(&As[r0][2 * t4 + 8]);
-            a[3] = *reinterpret_cast<const uint32_t*>(&As[r0 + 8][2 * t4 + 8]);
-#pragma unroll
-            for (int j = 0; j < BN / 8; ++j) {
-                uint32_t b[2];
-                b[0] = *reinterpret_cast<const uint32_t*>(&Bs[j * 8 + g][2 * t4]);
-                b[1] = *reinterpret_cast<const uint32_t*>(&Bs[j * 8 + g][2 * t4 + 8]);
-                mma_bf16(acc[j], a, b);
-            }
-            __syncthreads();
-        }
-    }
-    // epilogue: rows warp*16 + g (+8), columns j*8 + 2 t4 (+1)
-#pragma unroll
-    for (int j = 0; j < BN / 8; ++j) {
-#pragma unroll
-        for (int hrow = 0; hrow < 2; ++hrow) {
-            const long long v = v0 + warp * 16 + g + hrow * 8;
-            const int co = co0 + j * 8 + 2 * t4;
-            if (v >= nvox || co >= cout) continue;
-            float o0 = acc[j][hrow * 2], o1 = acc[j][hrow * 2 + 1];
-            if (bias) { o0 += bias[co]; o1 += bias[co + 1]; }
-            if (relu) { o0 = fmaxf(o0, 0.f); o1 = fmaxf(o1, 0.f); }
-            if (yf) {
-                float* p = yf + v * ldy + yoff + co;
-                if (accumulate) { p[0] += o0; p[1] += o1; }
-                else { p[0] = o0; p[1] = o1; }
-            } else {
-                *reinterpret_cast<__nv_bfloat162*>(y + v * ldy + yoff + co) = __floats2bfloat162_rn(o0, o1);
-            }
-        }
-    }
 }
 
 // Weight gradient for one tap per blockIdx.y: dW[t][co][ci] += sum over the block's voxel chunk of
@@ -410,30 +323,6 @@ bool aligned8(int a) { return (a % 8) == 0; }
 using bf16 = __nv_bfloat16;
 
 extern "C" {
-
-pf_status pfnn_conv3d(const void* x, int ldx, int xoff, const void* w, int cin, int cout, const float* bias, int relu,
-                      int flip, void* y_bf16, float* y_f32, int ldy, int yoff, int accumulate, int n, int d, int h,
-                      int wd, void* stream) {
-    if (!x || !w || (!y_bf16 && !y_f32) || n < 1 || d < 1 || h < 1 || wd < 1) return PF_E_INVALID;
-    if (cin < 16 || cin % 16 || cout < 8 || cout % 8 || !aligned8(ldx) || !aligned8(xoff) || ldy % 2 || yoff % 2)
-        return PF_E_INVALID;
-    const long long nvox = (long long)n * d * h * wd;
-    const int bn = cout >= 64 ? 64 : (cout > 16 ? 32 : 16);
-    if (cout > 16 && cout < 64 && cout != 32) return PF_E_INVALID;
-    dim3 grid((unsigned)((nvox + BM - 1) / BM), (unsigned)((cout + bn - 1) / bn));
-    cudaStream_t s = (cudaStream_t)stream;
-    if (bn == 64)
-        k_conv_gemm<64><<<grid, NTHR, 0, s>>>((const bf16*)x, ldx, xoff, (const bf16*)w, cin, cout, bias, relu, flip,
-                                              (bf16*)y_bf16, y_f32, ldy, yoff, accumulate, d, h, wd, nvox);
-    else if (bn == 32)
-        k_conv_gemm<32><<<grid, NTHR, 0, s>>>((const bf16*)x, ldx, xoff, (const bf16*)w, cin, cout, bias, relu, flip,
-                                              (bf16*)y_bf16, y_f32, ldy, yoff, accumulate, d, h, wd, nvox);
-    else
-        k_conv_gemm<16><<<grid, NTHR, 0, s>>>((const bf16*)x, ldx, xoff, (const bf16*)w, cin, cout, bias, relu, flip,
-                                              (bf16*)y_bf16, y_f32, ldy, yoff, accumulate, d, h, wd, nvox);
-    pfgb::count_launch();
-    return cudaGetLastError() == cudaSuccess ? PF_OK : PF_E_CUDA;
-}
 
 pf_status pfnn_conv3d_wgrad(const void* dy, int lddy, int dyoff, int cout, const void* x, int ldx, int xoff, int cin,
                             float* dw, int n, int d, int h, int wd, void* stream) {

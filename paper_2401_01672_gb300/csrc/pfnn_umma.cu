@@ -1,0 +1,409 @@
+// 3x3x3 convolution (forward and backward-data) of the learned warm start as an implicit GEMM on
+// the fifth-generation tensor cores of sm_103a: TMA brings the operand tiles into shared memory,
+// tcgen05.mma accumulates in tensor memory (TMEM), tcgen05.ld reads the accumulator back for the
+// epilogue.
+//
+// GEMM view (forward): D[v][co] = sum over taps t and input channels ci of X[v + off(t)][ci] W[t][co][ci]
+//   M = 128 voxels of one brick (wb x hb x db cells of one sample), N = cout, K = 27 taps x cin.
+// Backward data is the same GEMM on dY with flipped taps and the transposed weights [27][cin][cout].
+//
+// A operand: one TMA box of the channels-last activation tensor per (tap, channel block): the brick
+// shifted by the tap offset, ck channels deep.  Cells outside the grid (the convolution's zero
+// padding) are filled with zeros by the TMA unit itself.  The box lands in shared memory as 128 rows
+// (voxels, x fastest) of ck bf16 channels, swizzled with the pattern whose span equals the row length
+// (32, 64 or 128 bytes), which is the K-major layout the MMA descriptors name.
+// B operand: the [cout][ck] weight slice of the same tap and channel block (K-major, same swizzle).
+//
+// Roles (4 warps): thread 0 issues the TMA loads into a ring of shared-memory stages, thread 32 issues
+// the MMAs (one per 16 channels) and commits each stage back to the producer, warp 2 owns the TMEM
+// allocation; all four warps then read the 128 x cout fp32 accumulator (warp w owns TMEM lanes
+// 32w..32w+31 = voxels 32w..32w+31 of the brick) and apply bias, ReLU and the bf16 or fp32 store.
+// Every wait on an mbarrier gives up after a bounded number of tries, records the failure in a device
+// flag (read by pfnn_status) and lets the block finish: no wait can hang the GPU.
+#include "../../include/pfnn.h"
+#include "pf_internal.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int UM = 128;     // MMA M: voxels per tile
+constexpr int UTHR = 128;   // threads per block (4 warps)
+constexpr long long WAIT_TRIES = 1LL << 24;
+
+__device__ int g_umma_status = 0;  // 0 = ok; 1 = an mbarrier wait gave up
+
+struct UmmaArgs {
+    int cin, cout, ck, nkb;       // channels in/out, channels per k block, k blocks per tap
+    int wb, hb, db;               // brick (wb * hb * db = 128)
+    int D, H, W;                  // grid of one sample
+    int tx, ty, tz;               // bricks per sample along x, y, z
+    int flip, relu, accumulate;
+    int stages;
+    unsigned a_bytes, stage_bytes;  // shared-memory footprint of the A tile and of one stage (1024-byte units)
+    unsigned tx_bytes;              // bytes the two TMA loads of one stage deliver
+    unsigned idesc;               // MMA instruction descriptor
+    unsigned long long desc_hi;   // constant high bits of the shared-memory descriptors
+    int tmem_cols;
+    const float* bias;
+    bf16* y;
+    float* yf;
+    int ldy, yoff;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Wait for the phase of the given parity to complete; false (and the device flag set) after WAIT_TRIES.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (long long it = 0; it < WAIT_TRIES; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    atomicExch(&g_umma_status, 1);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1,
+                                            int c2, int c3, int c4) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, "
+        "%6, %7}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+        "[%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: start address (bits 0-13, in 16-byte units) over the constant
+// part (stride between 8-row groups, descriptor version, swizzle mode).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, unsigned long long hi) {
+    return hi | (uint64_t)((addr >> 4) & 0x3FFFu);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive on the mbarrier once every MMA issued so far by this thread has completed.
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__global__ void __launch_bounds__(UTHR)
+k_conv_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const UmmaArgs p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // stage tiles start on 1024-byte boundaries of the shared window (the swizzle patterns repeat there)
+    unsigned char* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    const int S = p.stages;
+    unsigned char* ctl = sm + (size_t)S * p.stage_bytes;  // barriers and the TMEM address slot
+    const uint32_t full0 = smem_u32(ctl);                  // full[s]  at full0  + 8 s
+    const uint32_t empty0 = full0 + 8u * S;                // empty[s] at empty0 + 8 s
+    const uint32_t accum = empty0 + 8u * S;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ctl + 16 * S + 8);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // brick of this block
+    long long b = blockIdx.x;
+    const int bx = (int)(b % p.tx);
+    b /= p.tx;
+    const int by = (int)(b % p.ty);
+    b /= p.ty;
+    const int bz = (int)(b % p.tz);
+    const int bn = (int)(b / p.tz);
+    const int x0 = bx * p.wb, y0 = by * p.hb, z0 = bz * p.db;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full0 + 8u * s, 1);
+            mbar_init(empty0 + 8u * s, 1);
+        }
+        mbar_init(accum, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(p.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const int KB = 27 * p.nkb;
+    const uint32_t sm0 = smem_u32(sm);
+
+    int issued = 0;  // TMA stages issued (thread 0)
+    if (threadIdx.x == 0) {
+        // ---- producer: one stage = the A box and the B slice of one (tap, channel block)
+        for (int kb = 0; kb < KB; ++kb, ++issued) {
+            const int s = kb % S;
+            const uint32_t use = (uint32_t)(kb / S);
+            if (kb >= S && !mbar_wait(empty0 + 8u * s, (use & 1u) ^ 1u)) break;
+            const uint32_t fb = full0 + 8u * s;
+            mbar_expect_tx(fb, p.tx_bytes);
+            const int tap = kb / p.nkb, cb = kb - tap * p.nkb;
+            int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+            if (p.flip) { dz = -dz; dy = -dy; dx = -dx; }
+            const uint32_t a_dst = sm0 + (uint32_t)s * p.stage_bytes;
+            tma_load_5d(a_dst, &tmA, fb, cb * p.ck, x0 + dx, y0 + dy, z0 + dz, bn);
+            tma_load_2d(a_dst + p.a_bytes, &tmB, fb, cb * p.ck, tap * p.cout);
+        }
+    } else if (threadIdx.x == 32) {
+        // ---- MMA issuer: ck / 16 MMAs (K = 16 each) per stage, accumulating into TMEM
+        bool ok = true;
+        for (int kb = 0; kb < KB && ok; ++kb) {
+            const int s = kb % S;
+            const uint32_t use = (uint32_t)(kb / S);
+            ok = mbar_wait(full0 + 8u * s, use & 1u);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_addr = sm0 + (uint32_t)s * p.stage_bytes;
+            const uint32_t b_addr = a_addr + p.a_bytes;
+            for (int k = 0; k < p.ck / 16; ++k) {
+                // K step k starts 32 bytes further along the (swizzled) rows
+                umma_f16(tmem, sdesc(a_addr + 32u * k, p.desc_hi), sdesc(b_addr + 32u * k, p.desc_hi), p.idesc,
+                         (kb > 0 || k > 0) ? 1u : 0u);
+            }
+            umma_commit(empty0 + 8u * s);
+        }
+        if (ok) umma_commit(accum);
+    }
+    __syncwarp();
+
+    // ---- epilogue: warp w reads TMEM lanes 32w..32w+31 (voxels of the brick), 16 columns at a time
+    const bool ready = mbar_wait(accum, 0u);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int m = warp * 32 + lane;
+    const int dx = m % p.wb, dy = (m / p.wb) % p.hb, dz = m / (p.wb * p.hb);
+    const int x = x0 + dx, y = y0 + dy, z = z0 + dz;
+    const bool inside = ready && x < p.W && y < p.H && z < p.D;
+    const long long v = (((long long)bn * p.D + z) * p.H + y) * p.W + x;
+    for (int c0 = 0; c0 < p.cout; c0 += 16) {
+        float o[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, o);  // whole warp, always
+        if (!inside) continue;
+        if (p.bias) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) o[q] += p.bias[c0 + q];
+        }
+        if (p.relu) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) o[q] = fmaxf(o[q], 0.f);
+        }
+        if (p.yf) {
+            float4* dst = reinterpret_cast<float4*>(p.yf + v * p.ldy + p.yoff + c0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float4 w = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+                if (p.accumulate) {
+                    const float4 r = dst[q];
+                    w.x += r.x; w.y += r.y; w.z += r.z; w.w += r.w;
+                }
+                dst[q] = w;
+            }
+        } else {
+            uint4 pk[2];
+            uint32_t* u = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(o[2 * q], o[2 * q + 1]);
+                u[q] = *reinterpret_cast<const uint32_t*>(&h2);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(p.y + v * p.ldy + p.yoff + c0);
+            dst[0] = pk[0];
+            dst[1] = pk[1];
+        }
+    }
+
+    // after a failed wait, the TMA loads still in flight must land before the block's shared memory
+    // is released (bounded as well); on success the completed accumulation implies that they have
+    if (threadIdx.x == 0 && !ready) {
+        for (int kb = issued - S < 0 ? 0 : issued - S; kb < issued; ++kb)
+            mbar_wait(full0 + 8u * (kb % S), (uint32_t)(kb / S) & 1u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 2) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+// swizzle span = row length of a k block (ck bf16 = 32, 64 or 128 bytes)
+CUtensorMapSwizzle tma_swizzle(int ck) {
+    return ck == 16 ? CU_TENSOR_MAP_SWIZZLE_32B : (ck == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B);
+}
+// the matching layout code of the MMA shared-memory descriptor (bits 61-63)
+unsigned long long umma_layout(int ck) { return ck == 16 ? 6ULL : (ck == 32 ? 4ULL : 2ULL); }
+
+unsigned round1024(unsigned v) { return (v + 1023u) & ~1023u; }
+
+}  // namespace
+
+extern "C" {
+
+pf_status pfnn_conv3d(const void* x, int ldx, int xoff, const void* w, int cin, int cout, const float* bias, int relu,
+                      int flip, void* y_bf16, float* y_f32, int ldy, int yoff, int accumulate, int n, int d, int h,
+                      int wd, void* stream) {
+    if (!x || !w || (!y_bf16 && !y_f32) || n < 1 || d < 1 || h < 1 || wd < 1) return PF_E_INVALID;
+    if (cin < 16 || cin % 16 || cout < 16 || cout % 16 || cout > 256 || ldx % 8 || xoff % 8 || ldx < xoff + cin ||
+        ldy % 8 || yoff % 8 || ldy < yoff + cout)
+        return PF_E_INVALID;
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(w) | reinterpret_cast<uintptr_t>(y_bf16) |
+         reinterpret_cast<uintptr_t>(y_f32)) % 16)
+        return PF_E_INVALID;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return PF_E_CUDA;
+
+    UmmaArgs a{};
+    a.cin = cin;
+    a.cout = cout;
+    a.ck = cin % 64 == 0 ? 64 : (cin % 32 == 0 ? 32 : 16);
+    a.nkb = cin / a.ck;
+    // brick of 128 cells: 32 x 4 x 1, 16 x 8 x 1 or 8 x 8 x 2 (x fastest), the widest that the grid fills
+    a.wb = wd >= 32 ? 32 : (wd >= 16 ? 16 : 8);
+    a.hb = a.wb == 32 ? 4 : 8;
+    a.db = UM / (a.wb * a.hb);
+    a.D = d;
+    a.H = h;
+    a.W = wd;
+    a.tx = (wd + a.wb - 1) / a.wb;
+    a.ty = (h + a.hb - 1) / a.hb;
+    a.tz = (d + a.db - 1) / a.db;
+    a.flip = flip;
+    a.relu = relu;
+    a.accumulate = accumulate;
+    a.a_bytes = round1024((unsigned)(UM * a.ck * 2));
+    a.stage_bytes = a.a_bytes + round1024((unsigned)(cout * a.ck * 2));
+    a.tx_bytes = (unsigned)((UM + cout) * a.ck * 2);
+    int stages = (int)(98304u / a.stage_bytes);
+    a.stages = stages < 2 ? 2 : (stages > 8 ? 8 : stages);
+    // instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A and B bf16 (bits 7-9, 10-12 = 1),
+    // both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+    a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(cout >> 3) << 17) | ((unsigned)(UM >> 4) << 24);
+    // descriptor: leading offset 16 B (unused for swizzled K-major), stride between 8-row groups = 8 rows x
+    // row bytes, version 1 (bit 46), swizzle layout code at bits 61-63
+    const unsigned long long sbo = (unsigned long long)(8 * a.ck * 2);
+    a.desc_hi = (1ULL << 16) | ((sbo >> 4) << 32) | (1ULL << 46) | (umma_layout(a.ck) << 61);
+    a.tmem_cols = cout <= 32 ? 32 : (cout <= 64 ? 64 : (cout <= 128 ? 128 : 256));
+    a.bias = bias;
+    a.y = (bf16*)y_bf16;
+    a.yf = y_f32;
+    a.ldy = ldy;
+    a.yoff = yoff;
+
+    alignas(64) CUtensorMap mA, mB;
+    {
+        const cuuint64_t dims[5] = {(cuuint64_t)cin, (cuuint64_t)wd, (cuuint64_t)h, (cuuint64_t)d, (cuuint64_t)n};
+        const cuuint64_t row = (cuuint64_t)ldx * 2;
+        const cuuint64_t strides[4] = {row, row * wd, row * wd * h, row * wd * h * d};
+        const cuuint32_t box[5] = {(cuuint32_t)a.ck, (cuuint32_t)a.wb, (cuuint32_t)a.hb, (cuuint32_t)a.db, 1};
+        const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+        if (enc(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)((const bf16*)x + xoff), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, tma_swizzle(a.ck), CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return PF_E_INVALID;
+    }
+    {
+        const cuuint64_t dims[2] = {(cuuint64_t)cin, (cuuint64_t)(27 * cout)};
+        const cuuint64_t strides[1] = {(cuuint64_t)cin * 2};
+        const cuuint32_t box[2] = {(cuuint32_t)a.ck, (cuuint32_t)cout};
+        const cuuint32_t es[2] = {1, 1};
+        if (enc(&mB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(w), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, tma_swizzle(a.ck), CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return PF_E_INVALID;
+    }
+    const size_t smem = (size_t)a.stages * a.stage_bytes + 1024 + 16 * a.stages + 16;
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_err = cudaFuncSetAttribute(k_conv_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024 + 2048);
+    });
+    if (attr_err != cudaSuccess) return PF_E_CUDA;
+    const long long blocks = (long long)a.tx * a.ty * a.tz * n;
+    if (blocks > 0x7FFFFFFFLL) return PF_E_RANGE;
+    k_conv_umma<<<(unsigned)blocks, UTHR, smem, (cudaStream_t)stream>>>(mA, mB, a);
+    pfgb::count_launch();
+    return cudaGetLastError() == cudaSuccess ? PF_OK : PF_E_CUDA;
+}
+
+pf_status pfnn_status(int* failed) {
+    if (!failed) return PF_E_INVALID;
+    int v = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&v, g_umma_status, sizeof(int)) != cudaSuccess) return PF_E_CUDA;
+    if (v && cudaMemcpyToSymbol(g_umma_status, &zero, sizeof(int)) != cudaSuccess) return PF_E_CUDA;
+    *failed = v;
+    return PF_OK;
+}
+
+}  // extern "C"

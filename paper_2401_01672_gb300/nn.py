@@ -71,6 +71,7 @@ def _lib():
             "pfnn_head_backward": [vp, i, vp, vp, ll, vp, vp, vp, vp],
             "pfnn_pack_input": [vp, vp, i, ll, ll, vp, vp],
             "pfnn_adam": [vp, vp, vp, vp, vp, ll, f, f, f, f, i, vp],
+            "pfnn_status": [C.POINTER(i)],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -87,6 +88,14 @@ def _ck(st, what):
 
 def _p(t):
     return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def check_device():
+    """Raise if a tensor-core convolution gave up a pipeline wait since the last check (synchronous)."""
+    flag = C.c_int(0)
+    _ck(_lib().pfnn_status(C.byref(flag)), "status")
+    if flag.value:
+        raise _pf.PfError(-2, "a tensor-core convolution gave up waiting for its pipeline; outputs are invalid")
 
 
 class UNet:

@@ -64,6 +64,7 @@ def train(G, feat, P, steps=600, batch=4, lr=2e-3, seed=0, log_every=0):
         if log_every and it % log_every == 0:
             hist.append((it, net.loss_value()))
     hist.append((steps, net.loss_value()))
+    NN.check_device()
     return net, hist
 
 
@@ -73,6 +74,7 @@ def predict(net, inst, G):
     Gd = torch.from_numpy(G.astype(np.float32)).cuda()
     feat = torch.tensor([NN.features(inst.dT, inst.sigma_scale)], dtype=torch.float32, device="cuda")
     prob = net.forward(Gd, feat)
+    NN.check_device()
     phi = prob.double().cpu().numpy()
     # cells with I_W = 0 never change (eq. water-indicator): keep their initial value
     frozen = (1.0 - inst.params["zeta"] * G) <= 0.0

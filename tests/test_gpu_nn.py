@@ -34,12 +34,24 @@ def relerr(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-30))
 
 
-@pytest.mark.parametrize("cin,cout", [(16, 16), (16, 32), (32, 16), (64, 128), (128, 64), (32, 8)])
-def test_conv_forward(env, cin, cout):
+def no_failed_waits(nn):
+    flag = nn.C.c_int(-1)
+    assert nn._lib().pfnn_status(nn.C.byref(flag)) == 0
+    return flag.value == 0
+
+
+# grid shapes choose the three brick shapes of the tensor-core tiles (x extent 9 -> 8 x 8 x 2,
+# 20 -> 16 x 8 x 1, 37 -> 32 x 4 x 1), each with ragged edges in every direction
+SHAPES = [(2, 6, 5, 9), (1, 3, 9, 20), (1, 2, 5, 37)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("cin,cout", [(16, 16), (16, 32), (32, 16), (64, 128), (128, 64), (48, 48), (32, 256)])
+def test_conv_forward(env, cin, cout, shape):
     torch, nn, O = env
     L = nn._lib()
     g = np.random.default_rng(cin * 7 + cout)
-    n, d, h, w = 2, 6, 5, 9
+    n, d, h, w = shape
     xt, x = bf(torch, g.standard_normal((n, d, h, w, cin)))
     wt, wv = bf(torch, g.standard_normal((27, cout, cin)) / math.sqrt(27 * cin))
     b = g.standard_normal(cout).astype(np.float32)
@@ -56,6 +68,19 @@ def test_conv_forward(env, cin, cout):
                          w, None) == 0
     torch.cuda.synchronize()
     assert relerr(yb.float().cpu().numpy(), ref) <= 8e-3
+    assert no_failed_waits(nn)
+
+
+def test_conv_rejects_unsupported(env):
+    """Sizes the tensor-core tiles do not take are refused on the host, before any launch."""
+    torch, nn, O = env
+    L = nn._lib()
+    x = torch.zeros((1, 4, 4, 8, 32), dtype=torch.bfloat16, device="cuda")
+    w = torch.zeros((27, 8, 32), dtype=torch.bfloat16, device="cuda")
+    y = torch.zeros((128, 16), dtype=torch.float32, device="cuda")
+    assert L.pfnn_conv3d(nn._p(x), 32, 0, nn._p(w), 32, 8, None, 0, 0, None, nn._p(y), 16, 0, 0, 1, 4, 4, 8, None) == -1
+    assert L.pfnn_conv3d(nn._p(x), 32, 0, nn._p(w), 32, 16, None, 0, 0, None, nn._p(y), 16, 4, 0, 1, 4, 4, 8, None) == -1
+    assert L.pfnn_conv3d(nn._p(x), 32, 0, nn._p(w), 24, 16, None, 0, 0, None, nn._p(y), 16, 0, 0, 1, 4, 4, 8, None) == -1
 
 
 def test_conv_channel_slices(env):
@@ -75,6 +100,7 @@ def test_conv_channel_slices(env):
     o = out.cpu().numpy()
     assert relerr(o[:, 8:24], ref) <= 2e-5
     assert np.all(o[:, :8] == 7.0) and np.all(o[:, 24:] == 7.0)
+    assert no_failed_waits(nn)
 
 
 @pytest.mark.parametrize("cin,cout", [(16, 16), (32, 64), (128, 64)])
@@ -97,6 +123,7 @@ def test_conv_backward_data_and_weight(env, cin, cout):
     torch.cuda.synchronize()
     assert relerr(dx.cpu().numpy(), O.conv3d_bwd_data(dy, wv).reshape(-1, cin)) <= 2e-5
     assert relerr(dw.cpu().numpy(), O.conv3d_bwd_weight(dy, x)) <= 2e-5
+    assert no_failed_waits(nn)
 
 
 def test_pool_upsample_head(env):
