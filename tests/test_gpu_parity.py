@@ -290,8 +290,9 @@ def test_error_statuses(torch_cuda):
 
 @pytest.mark.slow
 def test_full_size_rhs_and_step_256(torch_cuda, orc):
-    """256^3 full model (the benchmark size and launch configuration): right-hand side and
-    one forced Merson step element by element against the oracle, random G/theta/phi."""
+    """256^3 full model (the benchmark size; the step in the autotuned launch configuration the bench
+    times): right-hand side and one forced Merson step element by element against the oracle, random
+    G/theta/phi."""
     torch = torch_cuda
     shape = (256, 256, 256)
     h = 3e-4
@@ -309,6 +310,7 @@ def test_full_size_rhs_and_step_256(torch_cuda, orc):
     del oth, oph, dth, dph
     dt = 0.01
     g.set_state(th, ph, 0.0, dt)
+    g.autotune(None)   # the launch configuration the bench times
     g.rkm_step(dt, 1.0, force_accept=True)
     gth, gph, _, _ = g.get_state()
     sth, sph, _ = o.rkm_step(G, th, ph, 0.0, dt)

@@ -106,3 +106,30 @@ def test_fp32_form_freeze_thaw_against_oracle(env):
     assert 0.0 < u_ref["uwc"] < 1.0 and u_ref["n_ice"] > 100
     assert dphi <= 1e-3
     assert duwc <= 5e-3
+
+
+@pytest.mark.slow
+def test_fp32_form_full_size_fixed_steps_256(env):
+    """256^3 full model (the benchmark size) in the autotuned launch configuration the bench times:
+    three forced Merson steps of the binary32 form against the binary64 oracle, every cell.  The
+    binary32 rounding of the stage inputs (ulp(5 K) = 4.8e-7) times the step's stencil factor
+    (kappa dt/h^2 x 12 ~ 1.6) bounds the error near 1e-6 per step; the bars are 1e-4 K and 1e-4."""
+    torch, pf, oracle = env
+    shape = (256, 256, 256)
+    h = 3e-4
+    p = I.default_params(xi=h, xi_G=0.4 * h, alpha=4.17e6, dirichlet_faces=I.FACE_ZP, theta_freeze=-5.0)
+    th, ph, G = I.random_fields(shape, 2025, theta_scale=2.0, smooth=1)
+    dt = 0.01
+    g = pf.Grid(shape, h, I.MODEL_FULL, I.REACT_SIGMAP1P, I.PREC_FP32, p)
+    g.set_glass(G)
+    g.set_state(th, ph, 0.0, dt)
+    g.autotune(None)
+    s = g.run_fixed(3, dt)
+    assert s["n_accepted"] == 3
+    gth, gph, _, _ = g.get_state()
+    g.close()
+    o = oracle.Oracle(shape, h, "full", "sigmap1p", p)
+    r = o.run(G, th, ph, 0.0, dt, 3 * dt, 1.0, 3, fixed=True)
+    assert r["n_accepted"] == 3
+    assert float(np.max(np.abs(gth - r["theta"]))) <= 1e-4
+    assert float(np.max(np.abs(gph - r["phi"]))) <= 1e-4
