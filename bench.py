@@ -62,6 +62,24 @@ TRAFFIC_F64_S5_PER_CELL = 161.7
 KERNEL_BYTES_F64_S5 = 160
 
 
+def shard(items, rank, world):
+    """Independent units (instances) of rank `rank` out of `world`: every unit exactly once."""
+    return items[rank::world]
+
+
+def reduce_over_ranks(dist, to_max, to_sum, device):
+    """(max over ranks of each value in to_max, sum over ranks of each value in to_sum); the
+    values themselves when dist is None (one process)."""
+    if dist is None:
+        return list(map(float, to_max)), list(map(float, to_sum))
+    import torch
+    mx = torch.tensor([float(v) for v in to_max], dtype=torch.float64, device=device)
+    sm = torch.tensor([float(v) for v in to_sum], dtype=torch.float64, device=device)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return [float(v) for v in mx.cpu()], [float(v) for v in sm.cpu()]
+
+
 def env_int(k, d):
     try:
         return int(os.environ.get(k, d))
@@ -237,12 +255,16 @@ def time_form(torch, pf, w, precision, steps, warmup, stream, tiles=None):
     return g, s, ms, launches, prof
 
 
-def run_sweep(args, rank, world):
+def run_sweep(args, rank, world, dist):
     """Time-to-solution of the micro-scale sweep: every instance runs to its equilibrium test
-    (ice count unchanged for the time a free front needs to cross 20 cells), its t_end = 4 L/(mu dT) or the attempt cap."""
+    (ice count unchanged for the time a free front needs to cross 20 cells), its t_end = 4 L/(mu dT) or the attempt cap.
+    Under N ranks the instances are sharded (independent problems, no data-path collective); the job's
+    time is the slowest rank's, counts are summed."""
     from paper_2401_01672_gb300 import sweep
     inst = I.sweep_instances(args.instances)
-    mine = inst[rank::world]       # instances are independent: shard them over ranks
+    mine = shard(inst, rank, world)
+    if dist:
+        dist.barrier()
     with ClockSampler(env_int("LOCAL_RANK", 0)) as clk:
         b = sweep.run_batched(mine, max_steps=args.max_steps, keep_phi=True)
     p = sweep.run_plain(mine, max_steps=args.max_steps, keep_phi=True)
@@ -251,19 +273,29 @@ def run_sweep(args, rank, world):
     att_b = sum(r["n_accepted"] + r["n_rejected"] for r in b["instances"])
     att_p = sum(r["n_accepted"] + r["n_rejected"] for r in p["instances"])
     cell_att_b = sum(int(np.prod(i.shape)) * (r["n_accepted"] + r["n_rejected"]) for i, r in zip(mine, b["instances"]))
+    eq_b = sum(r["equilibrium"] for r in b["instances"])
+    eq_p = sum(r["equilibrium"] for r in p["instances"])
+    def nan_low(v):   # a rank with nothing to compare reports NaN: keep it out of the maximum
+        return v if v == v else -math.inf
+
+    (wall_b, wall_p, uwc_d, dphi_d), (cells, att_b, att_p, cell_att_b, eq_b, eq_p, n_eq) = reduce_over_ranks(
+        dist, [b["wall_s"], p["wall_s"], nan_low(acc["max_uwc_rel_diff"]), nan_low(acc["max_abs_dphi_at_equilibrium"])],
+        [cells, att_b, att_p, cell_att_b, eq_b, eq_p, acc["instances_in_equilibrium_both"]], "cuda")
+    acc = {"max_uwc_rel_diff": uwc_d if uwc_d > -math.inf else math.nan,
+           "max_abs_dphi_at_equilibrium": dphi_d if dphi_d > -math.inf else math.nan,
+           "instances_in_equilibrium_both": int(n_eq)}
     if rank == 0:
-        line = {"metric": "sweep time-to-solution (equilibrium, t_end or cap)", "value": b["wall_s"], "unit": "s",
+        line = {"metric": "sweep time-to-solution (equilibrium, t_end or cap)", "value": wall_b, "unit": "s",
                 "higher_is_better": False, "n_gpus": world, "steps": args.max_steps, "warmup": 0,
                 "dtype": "f32 fields / f64 control", "data": "synthetic", "scaling": "weak",
-                "config": {"workload": f"micro_sweep_{len(inst)}", "instances": len(mine), "cells": cells,
-                           "sizes": [i.shape[0] for i in mine], "cap": args.max_steps, "tol": 1e-6},
-                "batched": {"wall_s": b["wall_s"], "attempts": att_b, "device_iterations": b["iterations"],
-                            "cell_stage_per_s": 5 * cell_att_b / b["wall_s"],
-                            "equilibrium": sum(r["equilibrium"] for r in b["instances"]),
+                "config": {"workload": f"micro_sweep_{len(inst)}", "instances": len(inst), "cells": int(cells),
+                           "sizes": [i.shape[0] for i in inst], "cap": args.max_steps, "tol": 1e-6,
+                           "instances_per_rank": len(mine)},
+                "batched": {"wall_s": wall_b, "attempts": int(att_b), "device_iterations": b["iterations"],
+                            "cell_stage_per_s": 5 * cell_att_b / wall_b, "equilibrium": int(eq_b),
                             "tiles_by_zc": b["tiles"][:4]},
-                "plain_fp64": {"wall_s": p["wall_s"], "attempts": att_p,
-                               "equilibrium": sum(r["equilibrium"] for r in p["instances"])},
-                "speedup_vs_plain_fp64": p["wall_s"] / b["wall_s"], "accuracy_vs_plain_fp64": acc,
+                "plain_fp64": {"wall_s": wall_p, "attempts": int(att_p), "equilibrium": int(eq_p)},
+                "speedup_vs_plain_fp64": wall_p / wall_b, "accuracy_vs_plain_fp64": acc,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
 
@@ -359,9 +391,6 @@ def main():
     from paper_2401_01672_gb300 import pf
 
     torch.cuda.set_device(local)
-    if args.workload == "sweep48":
-        run_sweep(args, rank, world)
-        return
     if args.workload == "warmstart":
         run_warmstart(args, rank, world)
         return
@@ -369,6 +398,11 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "sweep48":
+        run_sweep(args, rank, world, dist)
+        if dist:
+            dist.destroy_process_group()
+        return
 
     w = make_workload(args.size)
     stream = torch.cuda.Stream()
@@ -402,14 +436,7 @@ def main():
     launches = pf.pf_kernel_launches() - l0
     attempts = s["n_accepted"] + s["n_rejected"]
     local_units = w.n_cells * 5 * attempts
-    ms_max = ms
-    units = local_units
-    if dist:
-        tt = torch.tensor([ms, float(local_units)], device="cuda", dtype=torch.float64)
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        ms_max, units = float(mx[0]), float(tt[1])
+    (ms_max,), (units,) = reduce_over_ranks(dist, [ms], [local_units], "cuda")
     value = units / (ms_max * 1e-3)
 
     # ---------------- dominant kernel, timed live with CUDA events on the launching stream
