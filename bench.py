@@ -300,6 +300,107 @@ def run_sweep(args, rank, world, dist):
         print(json.dumps(line), flush=True)
 
 
+# The paper's Table 3: wall-clock of its whole macro runs (10 h of physical time) on CPU nodes with
+# two 16-core AMD EPYC 7281 each (hybrid MPI/OpenMP), hours:minutes -> seconds.
+PAPER_TABLE3 = {
+    100: {"cores": 32, "sigmap1p_large": 71 * 60, "sigmap1p_small": 75 * 60, "gradp_large": 162 * 60,
+          "temp_gamma2": 23 * 60},
+    200: {"cores": 128, "sigmap1p_large": 549 * 60, "sigmap1p_small": 520 * 60, "gradp_large": 613 * 60,
+          "temp_gamma2": 566 * 60},
+    400: {"cores": 384, "sigmap1p_small": 5431 * 60, "temp_gamma2": 4457 * 60},
+}
+MACRO_CASES = {
+    "sigmap1p_large": (I.MODEL_FULL, I.REACT_SIGMAP1P, "large", 2.0),
+    "sigmap1p_small": (I.MODEL_FULL, I.REACT_SIGMAP1P, "small", 2.0),
+    "sigmap1p_tiny": (I.MODEL_FULL, I.REACT_SIGMAP1P, "tiny", 2.0),
+    "gradp_large": (I.MODEL_FULL, I.REACT_GRADP, "large", 2.0),
+    "gradp_small": (I.MODEL_FULL, I.REACT_GRADP, "small", 2.0),
+    "temp_gamma2": (I.MODEL_TEMP, I.REACT_SIGMAP1P, "large", 2.0),
+    "temp_gamma10": (I.MODEL_TEMP, I.REACT_SIGMAP1P, "large", 10.0),
+}
+
+
+def run_macro(args, rank, world):
+    """The paper's macro-scale parametric study (Sec. 3.1-3.2) on the vessel at N3 cells: 5 h cooling
+    through the cap at -25 K, 5 h heating at +20 K, binary64, tol 1e-6.  Reports each run's wall time
+    next to the paper's Table 3 (its CPU cluster; context) and the qualitative findings the paper
+    states about the ice-fraction curves.  Rank 0 only (one run = one GPU)."""
+    if rank != 0:
+        return
+    from paper_2401_01672_gb300 import macro, pf
+    names = list(MACRO_CASES) if args.macro_cases == "all" else args.macro_cases.split(",")
+    runs = {}
+    with ClockSampler(env_int("LOCAL_RANK", 0)) as clk:
+        for nm in names:
+            model, rx, sigma, gamma = MACRO_CASES[nm]
+            w = I.macro_case(args.macro_n3, model, rx, sigma=sigma, gamma=gamma)
+            runs[nm] = macro.run_case(w, max_attempts=args.macro_cap)
+            print(json.dumps({"case": nm, "status": runs[nm]["status"], "wall_s": runs[nm]["wall_s"],
+                              "attempts": runs[nm]["attempts"]}), file=sys.stderr, flush=True)
+    # water above the bead bed, as a share of all water: the ice fraction at which a front coming down
+    # from the cap reaches the bed
+    w0 = I.macro_case(args.macro_n3, I.MODEL_FULL)
+    g = pf.Grid(w0.shape, w0.h, w0.model, w0.reaction, I.PREC_FP64, w0.params)
+    g.set_geometry(w0.spheres, w0.x3_cap)
+    G = g.get_glass().reshape(w0.shape[2], -1)
+    g.close()
+    z = (np.arange(w0.shape[2]) + 0.5) * w0.h
+    water = G < 0.5
+    above = float(water[z > w0.extra["bed_top"]].sum() / water.sum())
+    summ = {nm: macro.summary(r) for nm, r in runs.items()}
+
+    def dist(a, b):
+        return macro.curve_distance(runs[a], runs[b]) if a in runs and b in runs else None
+
+    def early(a, b):   # largest difference while both fronts, coming down from the cap, are above the bed
+        if a not in runs or b not in runs:
+            return None
+
+        def cooling_above(r):
+            return {round(p["t"], 6): p["ice_fraction"] for p in r["curve"]
+                    if p["t"] <= I.MACRO_T_FREEZE and p["ice_fraction"] < above}
+        ca, cb = cooling_above(runs[a]), cooling_above(runs[b])
+        d = [abs(v - cb[t]) for t, v in ca.items() if t in cb]
+        return max(d) if d else None
+
+    def tf(nm, key):
+        return summ[nm][key] if nm in summ else None
+
+    checks = {
+        "models_agree_before_bed (max |diff| while the front is above the bed)":
+            {"sigmap1p_small_vs_temp": early("sigmap1p_small", "temp_gamma2"),
+             "sigmap1p_large_vs_temp": early("sigmap1p_large", "temp_gamma2")},
+        "large_sigma_freezes_later (t_half_freeze large >= small >= tiny)":
+            [tf("sigmap1p_large", "t_half_freeze_s"), tf("sigmap1p_small", "t_half_freeze_s"),
+             tf("sigmap1p_tiny", "t_half_freeze_s")],
+        "large_sigma_thaws_earlier (t_half_thaw large <= small <= tiny)":
+            [tf("sigmap1p_large", "t_half_thaw_s"), tf("sigmap1p_small", "t_half_thaw_s"),
+             tf("sigmap1p_tiny", "t_half_thaw_s")],
+        "sigmap1p_approaches_temp_as_sigma_decreases (max |diff| to Temp: large, small, tiny)":
+            [dist("sigmap1p_large", "temp_gamma2"), dist("sigmap1p_small", "temp_gamma2"),
+             dist("sigmap1p_tiny", "temp_gamma2")],
+        "temp_gamma_insensitive (max |diff| gamma 2 vs 10)": dist("temp_gamma2", "temp_gamma10"),
+        "gradp (status, max phi)": {nm: [runs[nm]["status"], summ[nm]["phi_max"]]
+                                    for nm in runs if nm.startswith("gradp")},
+    }
+    paper = PAPER_TABLE3.get(args.macro_n3, {})
+    headline = "sigmap1p_small" if "sigmap1p_small" in runs else names[0]
+    line = {"metric": "macro freeze-thaw run wall time (10 h physical)", "value": runs[headline]["wall_s"],
+            "unit": "s", "higher_is_better": False, "n_gpus": 1, "steps": runs[headline]["attempts"], "warmup": 0,
+            "dtype": "f64", "data": "synthetic", "scaling": "weak",
+            "config": {"workload": f"macro_vessel_n3_{args.macro_n3}", "grid": list(w0.shape), "h_m": w0.h,
+                       "beads": w0.extra["n_spheres"], "bed_top_m": w0.extra["bed_top"], "tol": 1e-6,
+                       "headline_case": headline},
+            "runs": {nm: {k: r[k] for k in ("status", "wall_s", "attempts", "accepted", "cells", "tiles_by_zc")}
+                     | {"cell_stage_per_s": 5 * r["cells"] * r["attempts"] / r["wall_s"] if r["wall_s"] else None}
+                     | summ[nm] for nm, r in runs.items()},
+            "paper_table3_s": paper, "water_above_bed_fraction": above, "qualitative_checks": checks,
+            "curves": {nm: [[round(p["t"], 3), round(p["ice_fraction"], 5)] for p in r["curve"]]
+                       for nm, r in runs.items()},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def run_warmstart(args, rank, world):
     """Learned warm start: equilibria of 64^3 instances from the batched solver -> BF16 encoder-decoder
     trained with the library's kernels -> inference on larger packings -> binary64 RKM relaxation to the
@@ -362,10 +463,15 @@ def main():
     ap.add_argument("--no-fp32-form", action="store_true")
     ap.add_argument("--tiles", type=int, nargs=2, metavar=("BY", "ZC"), default=None,
                     help="fixed tile shape (block height, z chunk) instead of the autotuner's choice")
-    ap.add_argument("--workload", default="full256", choices=["full256", "sweep48", "warmstart"],
+    ap.add_argument("--workload", default="full256", choices=["full256", "sweep48", "warmstart", "macro"],
                     help="full256: the binary64 bead workload (default); sweep48: the 48-instance micro-scale "
                          "sweep, batched binary32 persistent run vs the plain binary64 method")
     ap.add_argument("--max-steps", type=int, default=600, help="sweep48: attempt cap per instance")
+    ap.add_argument("--macro-n3", type=int, default=100, help="macro: cells along the vessel height (100/200/400)")
+    ap.add_argument("--macro-cap", type=int, default=1_500_000, help="macro: attempt cap per run")
+    ap.add_argument("--macro-cases", default="all",
+                    help="macro: comma-separated subset of sigmap1p_large,sigmap1p_small,sigmap1p_tiny,"
+                         "gradp_large,gradp_small,temp_gamma2,temp_gamma10")
     ap.add_argument("--instances", type=int, default=48, help="sweep48: number of instances")
     ap.add_argument("--train-samples", type=int, default=2000, help="warmstart: 64^3 training equilibria")
     ap.add_argument("--train-steps", type=int, default=1500, help="warmstart: Adam steps")
@@ -393,6 +499,9 @@ def main():
     torch.cuda.set_device(local)
     if args.workload == "warmstart":
         run_warmstart(args, rank, world)
+        return
+    if args.workload == "macro":
+        run_macro(args, rank, world)
         return
     dist = None
     if world > 1:

@@ -359,3 +359,76 @@ def warmstart_instances(n, side=64, seed=20240109, h=1e-7, solid=0.5, dT_range=(
         out.append(SweepInstance(shape, h, p, sp, phi0.ravel(), 0.1 * p["alpha"] * h * h,
                                  4 * side * h / (p["mu"] * dT), 20 * h / (p["mu"] * dT), sc, dT))
     return out
+
+
+# ------------------------------------------------------------------ macro-scale vessel (Sec. 3.1)
+# Table 2: vessel interior L3 x L3/2 x L3/2 with L3 = 6 cm, glass cap above 11/12 L3, bead radius
+# L3/20, xi_G = L3/500, xi = L3/N3, cooled through the cap at -25 K for 5 h, then heated at +20 K
+# for 5 h, initial temperature +20 K, nucleation disk of eq. (nucleation-site).
+MACRO_L3 = 0.06
+MACRO_T_FREEZE = 5 * 3600.0
+MACRO_T_END = 10 * 3600.0
+
+
+def settled_bed(L1, L2, r, bed_top, seed, candidates=64, max_fails=200):
+    """Stand-in for the paper's DEM-settled bead bed (the DEM positions are not available).  Spheres of
+    radius r are added one at a time: each of `candidates` uniformly random (x1, x2) positions inside
+    the walls is given the height where a vertically falling sphere first touches the floor or an
+    earlier sphere, and the lowest of them is taken (a sphere settles into the deepest pocket within
+    reach).  A sphere is kept if its top stays below bed_top; the bed is complete after max_fails
+    consecutive sets of candidates that are not.  Returns (n, 4) rows (x, y, z, r) in metres."""
+    g = rng(seed)
+    cs = np.zeros((0, 3))
+    fails = 0
+    while fails < max_fails:
+        x = g.uniform(r, L1 - r, candidates)
+        y = g.uniform(r, L2 - r, candidates)
+        z = np.full(candidates, r)
+        if len(cs):
+            d2 = (cs[None, :, 0] - x[:, None]) ** 2 + (cs[None, :, 1] - y[:, None]) ** 2
+            rest = np.where(d2 < 4.0 * r * r, cs[None, :, 2] + np.sqrt(np.maximum(4.0 * r * r - d2, 0.0)), r)
+            z = np.maximum(z, rest.max(axis=1))
+        q = int(np.argmin(z))
+        if z[q] + r <= bed_top:
+            cs = np.vstack([cs, [x[q], y[q], z[q]]])
+            fails = 0
+        else:
+            fails += 1
+    return np.hstack([cs, np.full((len(cs), 1), r)])
+
+
+def nucleation_disk(shape, h, L1, L2, L3) -> np.ndarray:
+    """Sharp 0/1 indicator of eq. (nucleation-site) at the cell centres: 0.87 L3 < x3 < 0.97 L3 and
+    (x1 - L1/2)^2 + (x2 - L2/2)^2 < (L1/3)^2."""
+    n1, n2, n3 = shape
+    x = (np.arange(n1) + 0.5) * h
+    y = (np.arange(n2) + 0.5) * h
+    z = (np.arange(n3) + 0.5) * h
+    rad = (x[None, None, :] - L1 / 2) ** 2 + (y[None, :, None] - L2 / 2) ** 2 < (L1 / 3) ** 2
+    slab = (z > 0.87 * L3) & (z < 0.97 * L3)
+    return (slab[:, None, None] & rad).astype(np.float64).ravel()
+
+
+def macro_case(n3, model, reaction=REACT_SIGMAP1P, sigma="large", gamma=2.0, seed=20240110, bed_fraction=0.6):
+    """The paper's macro-scale vessel (Table 2) on N3 = n3 cells along x3 (n1 = n2 = n3/2, h = L3/n3).
+    Phase-field models: alpha of the sigma class, zeta = 2, nucleation disk; Temp model: zeta = 1,
+    gamma as given, no phase-field state.  The bead bed fills the vessel up to bed_fraction L3."""
+    if n3 % 2:
+        raise ValueError("n3 must be even")
+    L3 = MACRO_L3
+    L1 = L2 = L3 / 2
+    h = L3 / n3
+    shape = (n3 // 2, n3 // 2, n3)
+    r = L3 / 20
+    spheres = settled_bed(L1, L2, r, bed_fraction * L3, seed)
+    temp = model == MODEL_TEMP
+    p = default_params(xi=L3 / n3, xi_G=L3 / 500, zeta=1.0 if temp else 2.0, gamma=gamma,
+                       alpha=ALPHA_MACRO[sigma], dirichlet_faces=FACE_ZP, theta_freeze=-25.0, theta_thaw=20.0,
+                       t_freeze=MACRO_T_FREEZE)
+    theta0 = np.full(int(np.prod(shape)), 20.0)
+    phi0 = None if temp else nucleation_disk(shape, h, L1, L2, L3)
+    tag = "temp" if temp else ("gradp" if reaction == REACT_GRADP else "sigmap1p")
+    name = f"macro{n3}_{tag}_" + (f"gamma{gamma:g}" if temp else sigma)
+    return Workload(name, shape, h, model, reaction, p, spheres, 11.0 / 12.0 * L3, theta0, phi0,
+                    extra={"n_spheres": len(spheres), "t_end": MACRO_T_END, "sigma": None if temp else sigma,
+                           "gamma": gamma if temp else None, "bed_top": bed_fraction * L3})

@@ -1,0 +1,41 @@
+"""Macro-scale vessel of Sec. 3.1 through the library on a coarse mesh (N3 = 40) for the first 40
+minutes of cooling: every model runs, the ice fraction grows once the cap is cold (the nucleation disk
+may first lose some ice to the +20 K water), SigmaP1-P keeps phi in [0, 1] to the step tolerance (its
+reaction term vanishes at 0 and 1), the Temp model's phi(theta) stays in [0, 1] by construction, and
+no temperature falls below the cap's."""
+import numpy as np
+import pytest
+
+from paper_2401_01672_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_01672_gb300 import build
+    build.build()
+    from paper_2401_01672_gb300 import macro
+    return macro
+
+
+@pytest.mark.parametrize("model,rx,sigma", [(I.MODEL_FULL, I.REACT_SIGMAP1P, "large"),
+                                            (I.MODEL_FULL, I.REACT_SIGMAP1P, "tiny"),
+                                            (I.MODEL_TEMP, I.REACT_SIGMAP1P, "large")])
+def test_macro_vessel_cooling(env, model, rx, sigma):
+    macro = env
+    w = I.macro_case(40, model, rx, sigma=sigma)
+    w.extra["t_end"] = 2400.0
+    r = macro.run_case(w, n_samples=12, max_attempts=200000)
+    assert r["status"] == "ok" and len(r["curve"]) == 12
+    ice = np.array([p["ice_fraction"] for p in r["curve"]])
+    assert np.all(np.diff(ice[len(ice) // 2:]) >= 0.0)
+    assert ice[-1] > ice[0] and ice[-1] > 0.0
+    lo = min(p["phi_min"] for p in r["curve"])
+    hi = max(p["phi_max"] for p in r["curve"])
+    assert lo >= -1e-6 and hi <= 1.0 + 1e-6
+    # the cap is the only cold boundary: the coldest temperature is the cap's
+    assert min(p["theta_min"] for p in r["curve"]) >= -25.0 - 1e-6
