@@ -401,6 +401,46 @@ def run_macro(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_uwc(args, rank, world):
+    """Micro-scale unfrozen water content against supercooling (Sec. 3.3) on an ordered (fcc-like) and a
+    random (settled) bead structure of radius 5 um: every (structure, dT) instance in one batched
+    binary32 run to its equilibrium test; UWC over the bottom half of the vessel.  The paper compares
+    its curves with measurements that are not available here; the bench reports the curves and the two
+    trends the paper states: UWC falls as the supercooling grows, and the structure with the larger void
+    fraction holds less unfrozen water.  Rank 0 only."""
+    if rank != 0:
+        return
+    from paper_2401_01672_gb300 import sweep
+    inst = I.uwc_instances(n3=args.uwc_n3)
+    with ClockSampler(env_int("LOCAL_RANK", 0)) as clk:
+        b = sweep.run_batched(inst, max_steps=args.max_steps)
+    curves, void = {}, {}
+    for i, r in zip(inst, b["instances"]):
+        curves.setdefault(i.label, []).append({"dT": i.dT, "uwc_percent": 100.0 * r["uwc"],
+                                               "equilibrium": bool(r["equilibrium"]), "t": r["t"],
+                                               "attempts": r["n_accepted"] + r["n_rejected"]})
+        if i.label not in void:
+            m = I.sharp_solid_mask(i.shape, i.spheres / i.h)[: i.shape[2] // 2]
+            void[i.label] = float(1.0 - m.mean())
+    mono = {k: all(a["uwc_percent"] >= c["uwc_percent"] for a, c in zip(v, v[1:])) for k, v in curves.items()}
+    labels = sorted(void, key=lambda k: void[k])   # denser structure first
+    order = None
+    if len(labels) == 2:
+        lo_void, hi_void = curves[labels[0]], curves[labels[1]]
+        order = all(h["uwc_percent"] <= l["uwc_percent"] for l, h in zip(lo_void, hi_void))
+    line = {"metric": "micro-scale UWC vs supercooling, batched time-to-equilibrium", "value": b["wall_s"], "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "steps": args.max_steps, "warmup": 0,
+            "dtype": "f32 fields / f64 control", "data": "synthetic", "scaling": "weak",
+            "config": {"workload": f"uwc_vs_dT_n3_{args.uwc_n3}", "instances": len(inst), "grid": list(inst[0].shape),
+                       "bead_radius_m": float(inst[0].spheres[0, 3]), "region": "bottom half",
+                       "void_fraction_bottom_half": void},
+            "batched": {"wall_s": b["wall_s"], "device_iterations": b["iterations"], "tiles_by_zc": b["tiles"][:2]},
+            "curves": curves,
+            "checks": {"uwc_falls_with_supercooling": mono, "larger_void_holds_less_unfrozen_water": order},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def run_warmstart(args, rank, world):
     """Learned warm start: equilibria of 64^3 instances from the batched solver -> BF16 encoder-decoder
     trained with the library's kernels -> inference on larger packings -> binary64 RKM relaxation to the
@@ -463,12 +503,13 @@ def main():
     ap.add_argument("--no-fp32-form", action="store_true")
     ap.add_argument("--tiles", type=int, nargs=2, metavar=("BY", "ZC"), default=None,
                     help="fixed tile shape (block height, z chunk) instead of the autotuner's choice")
-    ap.add_argument("--workload", default="full256", choices=["full256", "sweep48", "warmstart", "macro"],
+    ap.add_argument("--workload", default="full256", choices=["full256", "sweep48", "warmstart", "macro", "uwc"],
                     help="full256: the binary64 bead workload (default); sweep48: the 48-instance micro-scale "
                          "sweep, batched binary32 persistent run vs the plain binary64 method")
-    ap.add_argument("--max-steps", type=int, default=600, help="sweep48: attempt cap per instance")
+    ap.add_argument("--max-steps", type=int, default=600, help="sweep48, uwc: attempt cap per instance")
     ap.add_argument("--macro-n3", type=int, default=100, help="macro: cells along the vessel height (100/200/400)")
     ap.add_argument("--macro-cap", type=int, default=1_500_000, help="macro: attempt cap per run")
+    ap.add_argument("--uwc-n3", type=int, default=200, help="uwc: cells along the vessel height")
     ap.add_argument("--macro-cases", default="all",
                     help="macro: comma-separated subset of sigmap1p_large,sigmap1p_small,sigmap1p_tiny,"
                          "gradp_large,gradp_small,temp_gamma2,temp_gamma10")
@@ -502,6 +543,9 @@ def main():
         return
     if args.workload == "macro":
         run_macro(args, rank, world)
+        return
+    if args.workload == "uwc":
+        run_uwc(args, rank, world)
         return
     dist = None
     if world > 1:

@@ -172,7 +172,7 @@ pf_status pf_set_tiles(pf_grid* g, int by, int zc);
 pf_status pf_get_tiles(pf_grid* g, int* by, int* zc);
 
 /* Tile autotuner: times the five stage kernels of one Merson attempt for by in {4, 8, 16} x zc in
- * {4, 8, 16, 32, 64} on the grid itself and keeps the fastest.  The step controller is not run, so the
+ * {2, 3, 4, 5, 6, 8, 10, 12, 16, 24, 32, 64} on the grid itself and keeps the fastest.  The step controller is not run, so the
  * state, time, step size and counters are unchanged (stage 5 writes only the spare state buffer).  cache_path (NULL = none) is a text file of
  * lines "n1xn2xn3/model/reaction/precision by zc ms"; a cached shape is reused without timing and new
  * results are appended.  Outputs may be NULL. */

@@ -1053,14 +1053,17 @@ pf_status pf_get_tiles(pf_grid* g, int* by, int* zc) {
 }
 
 static const int kTuneBY[3] = {4, 8, 16};
-static const int kTuneZC[5] = {4, 8, 16, 32, 64};
+// z chunks: powers of two plus the values between them that let small grids fill the SMs in about one
+// wave of blocks (a 50 x 50 x 100 grid in 32 x 4 columns: zc = 5 gives 520 blocks, zc = 4 gives 650)
+constexpr int NZC = 12;
+static const int kTuneZC[NZC] = {2, 3, 4, 5, 6, 8, 10, 12, 16, 24, 32, 64};
 
 // Time the plain right-hand side (the stage kernels' common body) for every (by, zc) candidate on the
 // grid itself; ms[b][z] = best of 3 launches (infinity for skipped candidates).
 // Device time of one Merson attempt's five stage kernels for every tile shape (best of three after
 // a warm-up).  The controller is not launched: the state, the time and the step counters stay as
 // they are (stage 5 writes only the spare state buffer), and the control block is restored after.
-static pf_status tune_table(pf_grid* g, double ms[3][5]) {
+static pf_status tune_table(pf_grid* g, double ms[3][NZC]) {
     pf_status s = sync_ctrl_to_host(g);
     if (s != PF_OK) return s;
     const Ctrl saved = *g->hctrl;
@@ -1079,7 +1082,7 @@ static pf_status tune_table(pf_grid* g, double ms[3][5]) {
     cudaError_t e = cudaSuccess;
     const int by0 = g->by, zc0 = g->zc;
     for (int b = 0; b < 3; ++b)
-        for (int z = 0; z < 5; ++z) {
+        for (int z = 0; z < NZC; ++z) {
             ms[b][z] = INFINITY;
             if (e != cudaSuccess) continue;
             if (kTuneZC[z] > 2 * g->n3 && z > 0) continue;
@@ -1144,11 +1147,11 @@ pf_status pf_autotune(pf_grid* g, const char* cache_path, int* by_out, int* zc_o
     double best = INFINITY;
     const std::string key = tune_key(g);
     if (!cache_lookup(cache_path, key, &by, &zc, &best)) {
-        double ms[3][5];
+        double ms[3][NZC];
         pf_status s = tune_table(g, ms);
         if (s != PF_OK) return s;
         for (int b = 0; b < 3; ++b)
-            for (int z = 0; z < 5; ++z)
+            for (int z = 0; z < NZC; ++z)
                 if (ms[b][z] < best) { best = ms[b][z]; by = kTuneBY[b]; zc = kTuneZC[z]; }
         cache_store(cache_path, key, by, zc, best);
     }
@@ -1355,15 +1358,15 @@ pf_grid* pf_batch_grid(pf_batch* b, int i) { return (b && i >= 0 && i < b->n) ? 
 pf_status pf_batch_autotune(pf_batch* b, const char* cache_path) {
     if (!b) return bfail(nullptr, PF_E_INVALID, "batch is NULL");
     // a common block height for the batched kernels, then the best z chunk per instance
-    std::vector<std::array<std::array<double, 5>, 3>> t(b->n);
+    std::vector<std::array<std::array<double, NZC>, 3>> t(b->n);
     double sum[3] = {0, 0, 0};
     for (int q = 0; q < b->n; ++q) {
-        double ms[3][5];
+        double ms[3][NZC];
         pf_status s = tune_table(b->g[q], ms);
         if (s != PF_OK) return bfail(b, s, b->g[q]->err);
         for (int bb = 0; bb < 3; ++bb) {
             double m = INFINITY;
-            for (int z = 0; z < 5; ++z) { t[q][bb][z] = ms[bb][z]; m = fmin(m, ms[bb][z]); }
+            for (int z = 0; z < NZC; ++z) { t[q][bb][z] = ms[bb][z]; m = fmin(m, ms[bb][z]); }
             sum[bb] += m;
         }
     }
@@ -1372,7 +1375,7 @@ pf_status pf_batch_autotune(pf_batch* b, const char* cache_path) {
     b->by = kTuneBY[bb];
     for (int q = 0; q < b->n; ++q) {
         int z = 0;
-        for (int k = 1; k < 5; ++k) if (t[q][bb][k] < t[q][bb][z]) z = k;
+        for (int k = 1; k < NZC; ++k) if (t[q][bb][k] < t[q][bb][z]) z = k;
         set_tiles_impl(b->g[q], b->by, kTuneZC[z]);
         cache_store(cache_path, tune_key(b->g[q]), b->by, kTuneZC[z], t[q][bb][z]);
     }

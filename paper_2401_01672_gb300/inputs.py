@@ -311,6 +311,9 @@ class SweepInstance:
     eq_window: float          # equilibrium: ice count unchanged for the time a free front (mu dT) crosses 20 cells
     sigma_scale: float
     dT: float
+    x3_cap: float = math.nan  # glass cap (nan = none)
+    region: tuple = None      # unfrozen-water region {i0, i1, j0, j1, k0, k1} (None = whole grid)
+    label: str = ""
 
 
 def sweep_instances(n=48, seed=20240108, h=1e-7, solid=0.60, sizes=None, seed_radius=4.0):
@@ -432,3 +435,55 @@ def macro_case(n3, model, reaction=REACT_SIGMAP1P, sigma="large", gamma=2.0, see
     return Workload(name, shape, h, model, reaction, p, spheres, 11.0 / 12.0 * L3, theta0, phi0,
                     extra={"n_spheres": len(spheres), "t_end": MACRO_T_END, "sigma": None if temp else sigma,
                            "gamma": gamma if temp else None, "bed_top": bed_fraction * L3})
+
+
+def fcc_bed(L1, L2, bed_top, r, seed, gap=0.02):
+    """Ordered bed: a face-centred cubic lattice of spheres of radius r with nearest-neighbour distance
+    2r(1 + gap), centred in the walls, every sphere whose top stays below bed_top kept, each moved by a
+    seeded random offset shorter than half the gap (so no two touch).  Returns (n, 4) rows in metres."""
+    g = rng(seed)
+    a = 2.0 * r * (1.0 + gap) * math.sqrt(2.0)          # cubic cell of the fcc lattice
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]]) * a
+    nx, ny, nz = int(L1 / a) + 2, int(L2 / a) + 2, int(bed_top / a) + 2
+    ijk = np.stack(np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij"), -1).reshape(-1, 3)
+    pts = (ijk[:, None, :] * a + basis[None, :, :]).reshape(-1, 3)
+    lo = np.array([r, r, r])
+    hi = np.array([L1 - r, L2 - r, bed_top - r])
+    best, best_pts = -1, None
+    for ox in np.linspace(0, a, 9, endpoint=False):      # lattice shift keeping the most spheres
+        for oy in np.linspace(0, a, 9, endpoint=False):
+            q = pts + np.array([ox, oy, 0.0]) + lo
+            keep = np.all((q >= lo) & (q <= hi), axis=1)
+            if keep.sum() > best:
+                best, best_pts = int(keep.sum()), q[keep]
+    jit = g.normal(size=best_pts.shape)
+    jit *= (0.49 * gap * r) / np.maximum(np.linalg.norm(jit, axis=1, keepdims=True), 1e-300) * g.uniform(0, 1, (len(jit), 1))
+    c = np.clip(best_pts + jit, lo, hi)
+    return np.hstack([c, np.full((len(c), 1), r)])
+
+
+def uwc_instances(dTs=(0.05, 0.1, 0.2, 0.5, 1.0, 2.0), beds=("fcc", "settled"), n3=200, r=5e-6, seed=20240111):
+    """Micro-scale unfrozen-water study (Sec. 3.3): the vessel of Table 2 scaled so that the bead radius
+    is r (L3 = 20 r: polystyrene, r = 5 um), constant supercooling dT (micro model), realistic alpha of
+    Table 1, ice from the nucleation disk, unfrozen water counted in the bottom half of the vessel (which
+    the bed fills).  One instance per (bed, dT); beds: "fcc" (ordered, dense) and "settled" (random,
+    looser).  t_end = 20 L3/(mu dT) is a backstop: the runs stop on the equilibrium test (ice count
+    unchanged for the time a free front needs to cross 20 cells)."""
+    L3 = 20.0 * r
+    L1 = L2 = L3 / 2
+    h = L3 / n3
+    shape = (n3 // 2, n3 // 2, n3)
+    out = []
+    for b, bed in enumerate(beds):
+        if bed == "fcc":
+            sp = fcc_bed(L1, L2, 0.6 * L3, r, seed + b)
+        else:
+            sp = settled_bed(L1, L2, r, 0.6 * L3, seed + b)
+        phi0 = nucleation_disk(shape, h, L1, L2, L3)
+        for dT in dTs:
+            p = default_params(xi=L3 / n3, xi_G=L3 / 500, zeta=2.0, theta_micro=-float(dT), alpha=TABLE1["alpha"])
+            v = p["mu"] * dT
+            out.append(SweepInstance(shape, h, p, sp, phi0, 0.1 * p["alpha"] * h * h, 20 * L3 / v, 20 * h / v, 1.0,
+                                     float(dT), x3_cap=11.0 / 12.0 * L3,
+                                     region=(0, shape[0], 0, shape[1], 0, n3 // 2), label=bed))
+    return out

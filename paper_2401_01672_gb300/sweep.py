@@ -22,15 +22,15 @@ EQ_REL_TOL = 1e-3
 
 def _grid(inst, precision, stream=None):
     g = pf.Grid(inst.shape, inst.h, I.MODEL_MICRO, I.REACT_SIGMAP1P, precision, inst.params, stream=stream)
-    g.set_geometry(inst.spheres)
+    g.set_geometry(inst.spheres, inst.x3_cap)
     g.set_state(None, inst.phi0, 0.0, inst.dt0)
     return g
 
 
-def _summary(res, grids, keep_phi):
+def _summary(res, grids, keep_phi, instances):
     out = []
-    for r, g in zip(res, grids):
-        u = g.unfrozen_fraction()
+    for r, g, inst in zip(res, grids, instances):
+        u = g.unfrozen_fraction(inst.region)
         d = dict(r)
         d.update(uwc=u["uwc"], n_ice=u["n_ice"], n_water=u["n_water"])
         if keep_phi:
@@ -50,7 +50,7 @@ def run_batched(instances, tol=1e-6, max_steps=1000, precision=I.PREC_FP32, tile
     res = b.run_to([i.t_end for i in instances], tol, max_steps, eq_window=[i.eq_window for i in instances],
                    eq_rel_tol=EQ_REL_TOL)
     wall = time.perf_counter() - t0
-    out = _summary(res, grids, keep_phi)
+    out = _summary(res, grids, keep_phi, instances)
     iters = b.iterations()
     b.close()
     return {"wall_s": wall, "instances": out, "iterations": iters, "tiles": tiles}
@@ -69,7 +69,7 @@ def run_plain(instances, tol=1e-6, max_steps=1000, precision=I.PREC_FP64, keep_p
         res = b.run_to([inst.t_end], tol, max_steps, eq_window=[inst.eq_window],
                        eq_rel_tol=EQ_REL_TOL)
         wall += time.perf_counter() - t0
-        out += _summary(res, [g], keep_phi)
+        out += _summary(res, [g], keep_phi, [inst])
         b.close()
     return {"wall_s": wall, "instances": out}
 

@@ -39,3 +39,16 @@ def test_macro_vessel_cooling(env, model, rx, sigma):
     assert lo >= -1e-6 and hi <= 1.0 + 1e-6
     # the cap is the only cold boundary: the coldest temperature is the cap's
     assert min(p["theta_min"] for p in r["curve"]) >= -25.0 - 1e-6
+
+
+def test_uwc_falls_with_supercooling_coarse(env):
+    """Micro-scale vessel (bead radius 5 um) on a coarse mesh: at the larger supercooling the ice
+    reaches into smaller pores (Gibbs-Thomson), so less water stays unfrozen in the bed."""
+    from paper_2401_01672_gb300 import sweep
+    inst = I.uwc_instances(dTs=(0.1, 2.0), beds=("settled",), n3=60)
+    b = sweep.run_batched(inst, max_steps=6000)
+    res = b["instances"]
+    assert all(r["status"] == 0 for r in res)
+    assert all(r["equilibrium"] for r in res)
+    u = [r["uwc"] for r in res]
+    assert 0.0 <= u[1] < u[0] <= 1.0

@@ -55,3 +55,36 @@ def test_macro_case_parameters_follow_table2():
     assert math.isclose(w.x3_cap, 11 / 12 * 0.06) and np.all(w.theta0 == 20.0)
     t = I.macro_case(100, I.MODEL_TEMP, gamma=10.0)
     assert t.phi0 is None and t.params["zeta"] == 1.0 and t.params["gamma"] == 10.0
+
+
+def test_fcc_bed_is_a_jittered_lattice():
+    L1 = L2 = 50e-6
+    r = 5e-6
+    top = 60e-6
+    gap = 0.02
+    sp = I.fcc_bed(L1, L2, top, r, seed=3, gap=gap)
+    c = sp[:, :3]
+    assert len(sp) > 60
+    assert np.all(c[:, :2] >= r) and np.all(c[:, 0] <= L1 - r) and np.all(c[:, 1] <= L2 - r)
+    assert np.all(c[:, 2] >= r) and np.all(c[:, 2] <= top - r)
+    d = np.sqrt(((c[:, None, :] - c[None, :, :]) ** 2).sum(-1))
+    np.fill_diagonal(d, np.inf)
+    nn = d.min(axis=1)
+    # no contacts; every sphere within the jitter of the lattice's nearest-neighbour distance
+    assert nn.min() > 2 * r
+    assert np.all(nn <= 2 * r * (1 + gap) + 0.98 * gap * r + 1e-12)
+    # 12 lattice neighbours for spheres away from the walls
+    inner = np.all((c > 3 * r) & (c < np.array([L1, L2, top]) - 3 * r), axis=1)
+    assert np.any(inner)
+    counts = (d[inner] < 2 * r * (1 + 2 * gap)).sum(axis=1)
+    assert np.all(counts == 12)
+
+
+def test_uwc_instances_region_and_time_scales():
+    ins = I.uwc_instances(dTs=(0.1, 1.0), beds=("fcc", "settled"), n3=60)
+    assert [i.label for i in ins] == ["fcc", "fcc", "settled", "settled"]
+    i = ins[1]
+    assert i.shape == (30, 30, 60) and i.region == (0, 30, 0, 30, 0, 30)
+    assert math.isclose(i.params["theta_micro"], -1.0) and i.params["alpha"] == I.TABLE1["alpha"]
+    v = i.params["mu"] * 1.0
+    assert math.isclose(i.eq_window, 20 * i.h / v) and math.isclose(i.t_end, 20 * 100e-6 / v)
