@@ -40,7 +40,17 @@
 
 namespace pfgb {
 
-__device__ __forceinline__ double dtanh(double x) { return tanh(x); }
+// tanh in binary64; for |x| >= 20 the result is +-1 exactly (1 - tanh|x| < 2 e^-40 is below half an
+// ulp of 1, 2^-54), decided on the bit pattern, so cells far from the melting point skip the call
+__device__ __forceinline__ double dtanh(double x) {
+    const long long b = __double_as_longlong(x);
+    const long long a = b & 0x7FFFFFFFFFFFFFFFLL;
+    if (a >= 0x4034000000000000LL) {                 // |x| >= 20, infinities and NaN
+        if (a > 0x7FF0000000000000LL) return x;      // NaN
+        return __longlong_as_double((b & (1LL << 63)) | 0x3FF0000000000000LL);
+    }
+    return tanh(x);
+}
 __device__ __forceinline__ float dtanh(float x) { return tanhf(x); }
 __device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
