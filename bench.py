@@ -422,7 +422,11 @@ def run_uwc(args, rank, world):
         if i.label not in void:
             m = I.sharp_solid_mask(i.shape, i.spheres / i.h)[: i.shape[2] // 2]
             void[i.label] = float(1.0 - m.mean())
-    mono = {k: all(a["uwc_percent"] >= c["uwc_percent"] for a, c in zip(v, v[1:])) for k, v in curves.items()}
+    # UWC falls with the supercooling and levels off at a few tenths of a percent at the largest ones;
+    # differences below FLOOR_TIE percentage points count as ties
+    FLOOR_TIE = 0.25
+    mono = {k: all(a["uwc_percent"] >= c["uwc_percent"] - FLOOR_TIE for a, c in zip(v, v[1:]))
+            for k, v in curves.items()}
     labels = sorted(void, key=lambda k: void[k])   # denser structure first
     order = None
     if len(labels) == 2:
@@ -436,7 +440,8 @@ def run_uwc(args, rank, world):
                        "void_fraction_bottom_half": void},
             "batched": {"wall_s": b["wall_s"], "device_iterations": b["iterations"], "tiles_by_zc": b["tiles"][:2]},
             "curves": curves,
-            "checks": {"uwc_falls_with_supercooling": mono, "larger_void_holds_less_unfrozen_water": order},
+            "checks": {"uwc_falls_with_supercooling (ties below 0.25 points)": mono,
+                       "larger_void_holds_less_unfrozen_water": order},
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
@@ -509,7 +514,7 @@ def main():
     ap.add_argument("--max-steps", type=int, default=600, help="sweep48, uwc: attempt cap per instance")
     ap.add_argument("--macro-n3", type=int, default=100, help="macro: cells along the vessel height (100/200/400)")
     ap.add_argument("--macro-cap", type=int, default=1_500_000, help="macro: attempt cap per run")
-    ap.add_argument("--uwc-n3", type=int, default=200, help="uwc: cells along the vessel height")
+    ap.add_argument("--uwc-n3", type=int, default=120, help="uwc: cells along the vessel height")
     ap.add_argument("--macro-cases", default="all",
                     help="macro: comma-separated subset of sigmap1p_large,sigmap1p_small,sigmap1p_tiny,"
                          "gradp_large,gradp_small,temp_gamma2,temp_gamma10")
