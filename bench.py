@@ -446,6 +446,67 @@ def run_uwc(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# Layers of the warm-start network timed by --workload conv: (label, samples, side, cin, cout); the first
+# four are the 256^3 inference levels, the last two the 64^3 training batches at the widest levels.
+CONV_LAYERS = [("infer_l0_256", 1, 256, 16, 16), ("infer_l1_128", 1, 128, 32, 32), ("infer_l2_64", 1, 64, 64, 64),
+               ("infer_l3_32", 1, 32, 128, 128), ("train_l2_32x8", 8, 32, 128, 64), ("train_l0_64x8", 8, 64, 32, 16)]
+
+
+def run_conv(args, rank, world):
+    """Forward 3x3x3 convolutions of the warm-start network on the tensor cores (tcgen05, TMA operands,
+    TMEM accumulators), bf16 in and out, fp32 accumulation: device time per layer with CUDA events on
+    the launching stream, TFLOP/s (2 x 27 x cin x cout flops per voxel) against the measured bf16 dense
+    peak.  Inputs of the larger layers exceed L2.  Rank 0 only."""
+    if rank != 0:
+        return
+    import torch
+    from paper_2401_01672_gb300 import nn
+    L = nn._lib()
+    peaks, kind = load_peaks()
+    stream = torch.cuda.Stream()
+    g = torch.Generator(device="cuda").manual_seed(SEED)
+    out = {}
+    with ClockSampler(env_int("LOCAL_RANK", 0)) as clk, torch.cuda.stream(stream):
+        for (label, n, side, cin, cout) in CONV_LAYERS:
+            nv = n * side ** 3
+            x = torch.randn((nv, cin), device="cuda", generator=g).to(torch.bfloat16)
+            w = (torch.randn((27, cout, cin), device="cuda", generator=g) * 0.05).to(torch.bfloat16)
+            b = torch.zeros(cout, device="cuda")
+            y = torch.empty((nv, cout), device="cuda", dtype=torch.bfloat16)
+            a = (nn._p(x), cin, 0, nn._p(w), cin, cout, nn._p(b), 1, 0, nn._p(y), None, cout, 0, 0, n, side, side, side,
+                 C_void(stream.cuda_stream))
+            for _ in range(max(3, args.warmup)):
+                nn._ck(L.pfnn_conv3d(*a), label)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = max(5, args.steps)
+            e0.record(stream)
+            for _ in range(reps):
+                L.pfnn_conv3d(*a)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            tf = 2.0 * 27 * cin * cout * nv / (ms * 1e-3) / 1e12
+            out[label] = {"samples": n, "side": side, "cin": cin, "cout": cout, "ms": ms, "tflops": tf,
+                          "frac_of_bf16_peak": tf / peaks["bf16_tflops"],
+                          "io_gbs": nv * (cin + cout) * 2 / (ms * 1e-3) / 1e9}
+        nn.check_device()
+    top = max(out, key=lambda k: out[k]["tflops"])
+    line = {"metric": "warm-start 3x3x3 convolution throughput (forward, tcgen05)", "value": out[top]["tflops"],
+            "unit": "TFLOP/s", "higher_is_better": True, "n_gpus": 1, "steps": max(5, args.steps),
+            "warmup": max(3, args.warmup), "dtype": "bf16 (fp32 accumulation)", "data": "synthetic", "scaling": "weak",
+            "config": {"workload": "warmstart_conv_layers", "best_layer": top},
+            "roofline": {"bound": "tensor", "kernel": "k_conv_umma", "achieved": out[top]["tflops"],
+                         "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                         "frac": out[top]["tflops"] / peaks["bf16_tflops"], "peak_source": kind, "traffic": None},
+            "layers": out, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def C_void(v):
+    import ctypes
+    return ctypes.c_void_p(v)
+
+
 def run_warmstart(args, rank, world):
     """Learned warm start: equilibria of 64^3 instances from the batched solver -> BF16 encoder-decoder
     trained with the library's kernels -> inference on larger packings -> binary64 RKM relaxation to the
@@ -508,7 +569,7 @@ def main():
     ap.add_argument("--no-fp32-form", action="store_true")
     ap.add_argument("--tiles", type=int, nargs=2, metavar=("BY", "ZC"), default=None,
                     help="fixed tile shape (block height, z chunk) instead of the autotuner's choice")
-    ap.add_argument("--workload", default="full256", choices=["full256", "sweep48", "warmstart", "macro", "uwc"],
+    ap.add_argument("--workload", default="full256", choices=["full256", "sweep48", "warmstart", "macro", "uwc", "conv"],
                     help="full256: the binary64 bead workload (default); sweep48: the 48-instance micro-scale "
                          "sweep, batched binary32 persistent run vs the plain binary64 method")
     ap.add_argument("--max-steps", type=int, default=600, help="sweep48, uwc: attempt cap per instance")
@@ -551,6 +612,9 @@ def main():
         return
     if args.workload == "uwc":
         run_uwc(args, rank, world)
+        return
+    if args.workload == "conv":
+        run_conv(args, rank, world)
         return
     dist = None
     if world > 1:
