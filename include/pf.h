@@ -231,8 +231,10 @@ pf_status pf_measure_peaks(double* fp64_tflops, double* fp32_tflops, double* cop
  * Scratch: a file-scope __device__ array of PF_NOALLOC_MAX_PARTIALS + 1 slots of 32 bytes (about
  * 512 KiB) that every GPU loading the library holds until the process exits.  Each block of the
  * reduction covers 16384 cells, so a region may hold at most PF_NOALLOC_MAX_PARTIALS * 16384 =
- * 2^28 cells; larger regions return PF_E_RANGE before any launch.  Bad pointers, sizes or regions
- * return PF_E_INVALID; CUDA failures PF_E_CUDA.  No cudaMalloc, cudaFree or allocating library call is
+ * 2^28 cells; larger regions return PF_E_RANGE before any launch.  Bad sizes or regions, and G or phi
+ * that is not device memory of the current device (checked with cudaPointerGetAttributes), return
+ * PF_E_INVALID; CUDA failures PF_E_CUDA.  The arrays' lengths cannot be checked here: each must hold
+ * n1*n2*n3 values.  No cudaMalloc, cudaFree or allocating library call is
  * made.  The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
  * that device current; make that first call before any stream capture.  All calls share the array
  * and every slot a call reads is written earlier in the same call; calls that overlap on the GPU

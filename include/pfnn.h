@@ -38,8 +38,16 @@ pf_status pfnn_conv3d(const void* x, int ldx, int xoff, const void* w, int cin, 
                       int wd, void* stream);
 
 /* Reads and clears the device flag of the tensor-core convolutions (1 = a pipeline wait gave up since
- * the last call, so some output was not written).  Synchronous: waits for the device. */
+ * the last call, so some output was not written).  Returns PF_E_TIMEOUT when the flag was set, PF_OK
+ * when not (PF_E_CUDA if it cannot be read).  Synchronous: waits for the device. */
 pf_status pfnn_status(int* failed);
+
+/* Test of the failure path (no counterpart in the paper): the NEXT pfnn_conv3d call withholds the TMA
+ * loads of pipeline stage `stage` (0 <= stage < 27 * cin / ck) and bounds every pipeline wait by `tries`
+ * (1 <= tries <= 2^24) instead of 2^24.  The waits for that stage then give up: the call finishes
+ * without storing its output, TMEM freed after every issued MMA has retired, and pfnn_status reports
+ * it.  The setting applies to one call only.  Nothing faults: the withheld stage is an empty wait. */
+pf_status pfnn_test_withhold_stage(int stage, long long tries);
 
 /* Weight gradient: dw[t][co][ci] += sum_v dy[v][co] x[v + off(t)][ci]  (fp32 atomics, split over voxels). */
 pf_status pfnn_conv3d_wgrad(const void* dy, int lddy, int dyoff, int cout, const void* x, int ldx, int xoff, int cin,

@@ -121,6 +121,18 @@ extern "C" pf_status pf_unfrozen_fraction_noalloc(const double* G, const double*
     const long long nb = n > 0 ? (n + NA_CELLS_PER_PART - 1) / NA_CELLS_PER_PART : 1;
     // the fixed scratch holds PF_NOALLOC_MAX_PARTIALS partials of NA_CELLS_PER_PART cells each
     if (nb > PF_NOALLOC_MAX_PARTIALS) return PF_E_RANGE;
+    // both arrays must be device memory of the current device (cudaPointerGetAttributes allocates nothing)
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PF_E_CUDA;
+    for (const double* ptr : {G, phi}) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+            cudaGetLastError();
+            return PF_E_INVALID;
+        }
+        if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev)
+            return PF_E_INVALID;
+    }
     NaPart* parts = nullptr;
     cudaError_t e = na_scratch_address(&parts);
     if (e != cudaSuccess) return PF_E_CUDA;

@@ -39,6 +39,11 @@ constexpr int UM = 128;     // MMA M: voxels per tile
 constexpr int UTHR = 128;   // threads per block (4 warps)
 constexpr long long WAIT_TRIES = 1LL << 24;
 
+// Test-only setting of the failure-path test, consumed by the next pfnn_conv3d call: the producer
+// withholds the TMA loads of one stage and every wait gives up after g_test_tries tries.
+static int g_test_withhold = -1;
+static long long g_test_tries = 0;
+
 __device__ int g_umma_status = 0;  // 0 = ok; 1 = an mbarrier wait gave up
 
 struct UmmaArgs {
@@ -48,6 +53,8 @@ struct UmmaArgs {
     int tx, ty, tz;               // bricks per sample along x, y, z
     int flip, relu, accumulate;
     int stages;
+    int withhold;                 // stage whose loads are withheld (test of the failure path), -1 = none
+    long long tries;              // bound of every mbarrier wait
     unsigned a_bytes, stage_bytes;  // shared-memory footprint of the A tile and of one stage (1024-byte units)
     unsigned tx_bytes;              // bytes the two TMA loads of one stage deliver
     unsigned idesc;               // MMA instruction descriptor
@@ -72,8 +79,8 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 }
 
 // Wait for the phase of the given parity to complete; false (and the device flag set) after WAIT_TRIES.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (long long it = 0; it < WAIT_TRIES; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long tries) {
+    for (long long it = 0; it < tries; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -151,6 +158,7 @@ k_conv_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const uint32_t empty0 = full0 + 8u * S;                // empty[s] at empty0 + 8 s
     const uint32_t accum = empty0 + 8u * S;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ctl + 16 * S + 8);
+    __shared__ int s_fail;  // the MMA issuer gave up a wait: the accumulator is incomplete
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -170,6 +178,7 @@ k_conv_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             mbar_init(empty0 + 8u * s, 1);
         }
         mbar_init(accum, 1);
+        s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 2) {
@@ -191,9 +200,10 @@ k_conv_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         for (int kb = 0; kb < KB; ++kb, ++issued) {
             const int s = kb % S;
             const uint32_t use = (uint32_t)(kb / S);
-            if (kb >= S && !mbar_wait(empty0 + 8u * s, (use & 1u) ^ 1u)) break;
+            if (kb >= S && !mbar_wait(empty0 + 8u * s, (use & 1u) ^ 1u, p.tries)) break;
             const uint32_t fb = full0 + 8u * s;
             mbar_expect_tx(fb, p.tx_bytes);
+            if (kb == p.withhold) continue;  // test of the failure path: this stage never fills
             const int tap = kb / p.nkb, cb = kb - tap * p.nkb;
             int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
             if (p.flip) { dz = -dz; dy = -dy; dx = -dx; }
@@ -207,7 +217,7 @@ k_conv_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         for (int kb = 0; kb < KB && ok; ++kb) {
             const int s = kb % S;
             const uint32_t use = (uint32_t)(kb / S);
-            ok = mbar_wait(full0 + 8u * s, use & 1u);
+            ok = mbar_wait(full0 + 8u * s, use & 1u, p.tries);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a_addr = sm0 + (uint32_t)s * p.stage_bytes;
@@ -219,12 +229,16 @@ k_conv_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             }
             umma_commit(empty0 + 8u * s);
         }
-        if (ok) umma_commit(accum);
+        // the accumulator barrier completes once every MMA issued above has retired, also after a
+        // failed wait: TMEM and the stages are not released while an MMA may still use them
+        if (!ok) s_fail = 1;
+        umma_commit(accum);
     }
     __syncwarp();
+    __syncthreads();  // s_fail is visible to every thread
 
     // ---- epilogue: warp w reads TMEM lanes 32w..32w+31 (voxels of the brick), 16 columns at a time
-    const bool ready = mbar_wait(accum, 0u);
+    const bool ready = mbar_wait(accum, 0u, p.tries) && !s_fail;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int m = warp * 32 + lane;
     const int dx = m % p.wb, dy = (m / p.wb) % p.hb, dz = m / (p.wb * p.hb);
@@ -272,7 +286,7 @@ k_conv_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     // is released (bounded as well); on success the completed accumulation implies that they have
     if (threadIdx.x == 0 && !ready) {
         for (int kb = issued - S < 0 ? 0 : issued - S; kb < issued; ++kb)
-            mbar_wait(full0 + 8u * (kb % S), (uint32_t)(kb / S) & 1u);
+            mbar_wait(full0 + 8u * (kb % S), (uint32_t)(kb / S) & 1u, p.tries);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -341,6 +355,10 @@ pf_status pfnn_conv3d(const void* x, int ldx, int xoff, const void* w, int cin, 
     a.tz = (d + a.db - 1) / a.db;
     a.flip = flip;
     a.relu = relu;
+    a.withhold = g_test_withhold;
+    a.tries = g_test_tries > 0 ? g_test_tries : WAIT_TRIES;
+    g_test_withhold = -1;
+    g_test_tries = 0;
     a.accumulate = accumulate;
     a.a_bytes = round1024((unsigned)(UM * a.ck * 2));
     a.stage_bytes = a.a_bytes + round1024((unsigned)(cout * a.ck * 2));
@@ -403,6 +421,13 @@ pf_status pfnn_status(int* failed) {
     if (cudaMemcpyFromSymbol(&v, g_umma_status, sizeof(int)) != cudaSuccess) return PF_E_CUDA;
     if (v && cudaMemcpyToSymbol(g_umma_status, &zero, sizeof(int)) != cudaSuccess) return PF_E_CUDA;
     *failed = v;
+    return v ? PF_E_TIMEOUT : PF_OK;
+}
+
+pf_status pfnn_test_withhold_stage(int stage, long long tries) {
+    if (stage < 0 || tries < 1 || tries > WAIT_TRIES) return PF_E_INVALID;
+    g_test_withhold = stage;
+    g_test_tries = tries;
     return PF_OK;
 }
 

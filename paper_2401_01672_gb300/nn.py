@@ -72,6 +72,7 @@ def _lib():
             "pfnn_pack_input": [vp, vp, i, ll, ll, vp, vp],
             "pfnn_adam": [vp, vp, vp, vp, vp, ll, f, f, f, f, i, vp],
             "pfnn_status": [C.POINTER(i)],
+            "pfnn_test_withhold_stage": [i, ll],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -93,9 +94,10 @@ def _p(t):
 def check_device():
     """Raise if a tensor-core convolution gave up a pipeline wait since the last check (synchronous)."""
     flag = C.c_int(0)
-    _ck(_lib().pfnn_status(C.byref(flag)), "status")
-    if flag.value:
-        raise _pf.PfError(-2, "a tensor-core convolution gave up waiting for its pipeline; outputs are invalid")
+    st = _lib().pfnn_status(C.byref(flag))
+    if st == _pf.PF_E_TIMEOUT or flag.value:
+        raise _pf.PfError(_pf.PF_E_TIMEOUT, "a tensor-core convolution gave up waiting for its pipeline; outputs are invalid")
+    _ck(st, "status")
 
 
 class UNet:

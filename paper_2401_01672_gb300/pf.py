@@ -428,6 +428,25 @@ def pf_measure_peaks():
     return a.value, b.value, c.value
 
 
+def _check_noalloc_arrays(G_dev, phi_dev, shape):
+    """Arguments of pf_unfrozen_fraction_noalloc: binary64 tensors of at least n1*n2*n3 elements on the
+    current CUDA device.  The kernel reads every cell of the grid's box, so a shorter or narrower array,
+    or one on another GPU, would be read out of bounds; raise ValueError before the call instead."""
+    n = int(shape[0]) * int(shape[1]) * int(shape[2])
+    for name, t in (("G", G_dev), ("phi", phi_dev)):
+        if t is None:
+            raise ValueError(f"{name} is required")
+        if str(t.dtype) != "torch.float64":
+            raise ValueError(f"{name} must be float64, got {t.dtype}")
+        if t.numel() < n:
+            raise ValueError(f"{name} has {t.numel()} elements, the grid needs {n}")
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA tensor")
+        import torch
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{torch.cuda.current_device()}")
+
+
 def pf_unfrozen_fraction_noalloc(G_dev, phi_dev, shape, region=None, stream=None):
     """Unfrozen-water counts on caller-owned device arrays, without any device allocation.
 
@@ -435,6 +454,7 @@ def pf_unfrozen_fraction_noalloc(G_dev, phi_dev, shape, region=None, stream=None
     module global).  Returns (status, dict); status is returned, not raised, so callers can
     tell PF_E_RANGE (region above the fixed scratch's limit) from other errors.
     """
+    _check_noalloc_arrays(G_dev, phi_dev, shape)
     lib = load_library()
     r = None if region is None else (C.c_int * 6)(*[int(v) for v in region])
     u, sm = C.c_double(), C.c_double()

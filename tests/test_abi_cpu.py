@@ -98,3 +98,16 @@ def test_missing_library_fails_loudly(tmp_path):
             pf.load_library(str(tmp_path / "nope.so"))
     finally:
         pf._lib = saved
+
+
+def test_noalloc_wrapper_refuses_arrays_it_would_overrun():
+    """pf_unfrozen_fraction_noalloc reads n1*n2*n3 binary64 values from each array: the binding refuses
+    narrower, shorter or host arrays before the C call (checked without a GPU)."""
+    torch = pytest.importorskip("torch")
+    from paper_2401_01672_gb300 import pf
+    good = torch.zeros(512, dtype=torch.float64)
+    for bad in (torch.zeros(512, dtype=torch.float32), torch.zeros(511, dtype=torch.float64), good, None):
+        with pytest.raises(ValueError):
+            pf.pf_unfrozen_fraction_noalloc(bad, good, (8, 8, 8))
+        with pytest.raises(ValueError):
+            pf.pf_unfrozen_fraction_noalloc(good, bad, (8, 8, 8))

@@ -36,8 +36,9 @@ def relerr(a, b):
 
 def no_failed_waits(nn):
     flag = nn.C.c_int(-1)
-    assert nn._lib().pfnn_status(nn.C.byref(flag)) == 0
-    return flag.value == 0
+    st = nn._lib().pfnn_status(nn.C.byref(flag))
+    assert st in (0, -7)
+    return st == 0 and flag.value == 0
 
 
 # grid shapes choose the three brick shapes of the tensor-core tiles (x extent 9 -> 8 x 8 x 2,
@@ -81,6 +82,35 @@ def test_conv_rejects_unsupported(env):
     assert L.pfnn_conv3d(nn._p(x), 32, 0, nn._p(w), 32, 8, None, 0, 0, None, nn._p(y), 16, 0, 0, 1, 4, 4, 8, None) == -1
     assert L.pfnn_conv3d(nn._p(x), 32, 0, nn._p(w), 32, 16, None, 0, 0, None, nn._p(y), 16, 4, 0, 1, 4, 4, 8, None) == -1
     assert L.pfnn_conv3d(nn._p(x), 32, 0, nn._p(w), 24, 16, None, 0, 0, None, nn._p(y), 16, 0, 0, 1, 4, 4, 8, None) == -1
+
+
+@pytest.mark.parametrize("stage", [0, 5, 26])
+def test_conv_gives_up_a_withheld_stage_and_recovers(env, stage):
+    """Failure path of the bounded pipeline waits: with the loads of one stage withheld (a wait that
+    nothing will complete; no bad access) and a short bound, the call finishes without storing,
+    pfnn_status reports PF_E_TIMEOUT once, and the next normal call is correct."""
+    torch, nn, O = env
+    L = nn._lib()
+    g = np.random.default_rng(11)
+    n, d, h, w, cin, cout = 1, 4, 8, 32, 16, 32
+    xt, x = bf(torch, g.standard_normal((n, d, h, w, cin)))
+    wt, wv = bf(torch, g.standard_normal((27, cout, cin)) / math.sqrt(27 * cin))
+    y = torch.full((n * d * h * w, cout), 3.0, dtype=torch.float32, device="cuda")
+    assert no_failed_waits(nn)
+    assert L.pfnn_test_withhold_stage(stage, 1 << 10) == 0
+    assert L.pfnn_conv3d(nn._p(xt), cin, 0, nn._p(wt), cin, cout, None, 0, 0, None, nn._p(y), cout, 0, 0, n, d, h, w,
+                         None) == 0
+    torch.cuda.synchronize()
+    flag = nn.C.c_int(0)
+    assert L.pfnn_status(nn.C.byref(flag)) == -7 and flag.value == 1
+    assert bool(torch.all(y == 3.0))          # nothing stored by the call that gave up
+    assert no_failed_waits(nn)                # the flag was cleared
+    assert L.pfnn_conv3d(nn._p(xt), cin, 0, nn._p(wt), cin, cout, None, 0, 0, None, nn._p(y), cout, 0, 0, n, d, h, w,
+                         None) == 0
+    torch.cuda.synchronize()
+    assert relerr(y.cpu().numpy(), O.conv3d(x, wv).reshape(-1, cout)) <= 2e-5
+    assert no_failed_waits(nn)
+    assert L.pfnn_test_withhold_stage(-1, 10) == -1
 
 
 def test_conv_channel_slices(env):

@@ -62,6 +62,22 @@ def test_noalloc_rejects_bad_arguments_and_oversize_regions(env):
     Gd = torch.zeros(512, dtype=torch.float64, device="cuda")
     st, _ = pf.pf_unfrozen_fraction_noalloc(Gd, Gd, shape, (0, 9, 0, 8, 0, 8))
     assert st == pf.PF_E_INVALID
+    # arrays the kernel would read out of bounds are refused before the call
+    for bad in (torch.zeros(512, dtype=torch.float32, device="cuda"),
+                torch.zeros(511, dtype=torch.float64, device="cuda"),
+                torch.zeros(512, dtype=torch.float64)):
+        with pytest.raises(ValueError):
+            pf.pf_unfrozen_fraction_noalloc(bad, Gd, shape)
+        with pytest.raises(ValueError):
+            pf.pf_unfrozen_fraction_noalloc(Gd, bad, shape)
+    # host memory handed to the C entry point directly is refused there (not device memory)
+    import ctypes as C
+    host = (C.c_double * 512)()
+    lib = pf.load_library()
+    nw = C.c_longlong(-1)
+    st = lib.pf_unfrozen_fraction_noalloc(C.cast(host, C.c_void_p), C.c_void_p(Gd.data_ptr()), 8, 8, 8, None, None,
+                                          None, None, C.byref(nw), None)
+    assert st == pf.PF_E_INVALID and nw.value == -1
     # 1024 x 1024 x 257 cells is above the 2^28-cell limit of the fixed scratch; the arrays are
     # really that large, so nothing could be read out of bounds even without the check.
     big = (1024, 1024, 257)
