@@ -33,15 +33,22 @@ REACTION = {"sigmap1p": 0, "gradp": 1}
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-O2 -ffp-contract=off, IEEE rounding as written)."""
+    """Compile the oracle with gcc (-O2 -ffp-contract=off, IEEE rounding as written), with OpenMP
+    over the loops on cells where the compiler has it (results do not depend on the thread count)."""
     if _OVERRIDE:
         return _OVERRIDE
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        if subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True).returncode != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def threads(n: int = 0) -> int:
+    """Threads of the oracle's loops over cells: n > 0 sets the count; returns the count in use."""
+    return int(_load().or_threads(int(n)))
 
 
 class ORModel(C.Structure):
@@ -76,6 +83,8 @@ def _load():
         lib.or_run.argtypes = [P(ORModel), pd, pd, pd, pd, pd, d, d, ll, i, pll, pll, pd, pd]
         lib.or_run.restype = i
         lib.or_uwc.argtypes = [P(ORModel), pd, pd, P(C.c_int), pll, pll, pd, pd]
+        lib.or_threads.argtypes = [i]
+        lib.or_threads.restype = i
         _lib = lib
     return _lib
 

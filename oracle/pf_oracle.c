@@ -37,11 +37,30 @@
  *     (decided by the step's start time: t < t_freeze -> freeze value);
  *   - E = max over cells and integrated fields of |dt/30 (2k1 - 9k3 + 8k4 - k5)|.
  *
- * Built with -O2 -ffp-contract=off so each operation rounds as written.
+ * Built with -O2 -ffp-contract=off so each operation rounds as written.  With -fopenmp the loops
+ * over cells are shared among threads (every cell is computed by the same arithmetic whatever the
+ * thread; the error maximum does not depend on the order in which cells are visited; the UWC sums
+ * stay serial and in a fixed order), so results are identical for any thread count.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads used by the loops over cells: n > 0 sets the count; returns the count in use (1 when
+ * built without OpenMP). */
+int or_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 enum { OR_FULL = 0, OR_TEMP = 1, OR_MICRO = 2 };
 enum { OR_SIGMAP1P = 0, OR_GRADP = 1 };
@@ -72,6 +91,7 @@ void or_glass(const or_model* m, const double* spheres, long long n_spheres, dou
 {
     long long N = (long long)m->n1 * m->n2 * m->n3;
     long long count = cells ? n_cells : N;
+#pragma omp parallel for schedule(static)
     for (long long q = 0; q < count; ++q) {
         long long id = cells ? cells[q] : q;
         long long i = id % m->n1;
@@ -171,6 +191,7 @@ void or_rhs(const or_model* m, const double* G, double t, const double* theta, c
     const long long stride[3] = {1, n1, (long long)n1 * n2};
     const int dims[3] = {n1, n2, n3};
 
+#pragma omp parallel for schedule(static)
     for (long long q = 0; q < count; ++q) {
         long long id = cells ? cells[q] : q;
         int idx[3];
@@ -287,24 +308,28 @@ void or_rkm_step(const or_model* m, const double* G, double t, double dt,
     /* stage 1 */
     or_rhs(m, G, t, yt, yp, NULL, 0, k[1][0], k[1][1]);
     /* stage 2 */
+#pragma omp parallel for schedule(static)
     for (long long q = 0; q < N; ++q) {
         if (ht) u_th[q] = y_th[q] + dt / 3.0 * k[1][0][q];
         if (hp) u_ph[q] = y_ph[q] + dt / 3.0 * k[1][1][q];
     }
     or_rhs(m, G, t, ht ? u_th : NULL, hp ? u_ph : NULL, NULL, 0, k[2][0], k[2][1]);
     /* stage 3 */
+#pragma omp parallel for schedule(static)
     for (long long q = 0; q < N; ++q) {
         if (ht) u_th[q] = y_th[q] + dt / 6.0 * k[1][0][q] + dt / 6.0 * k[2][0][q];
         if (hp) u_ph[q] = y_ph[q] + dt / 6.0 * k[1][1][q] + dt / 6.0 * k[2][1][q];
     }
     or_rhs(m, G, t, ht ? u_th : NULL, hp ? u_ph : NULL, NULL, 0, k[3][0], k[3][1]);
     /* stage 4 */
+#pragma omp parallel for schedule(static)
     for (long long q = 0; q < N; ++q) {
         if (ht) u_th[q] = y_th[q] + dt / 8.0 * k[1][0][q] + 3.0 * dt / 8.0 * k[3][0][q];
         if (hp) u_ph[q] = y_ph[q] + dt / 8.0 * k[1][1][q] + 3.0 * dt / 8.0 * k[3][1][q];
     }
     or_rhs(m, G, t, ht ? u_th : NULL, hp ? u_ph : NULL, NULL, 0, k[4][0], k[4][1]);
     /* stage 5 */
+#pragma omp parallel for schedule(static)
     for (long long q = 0; q < N; ++q) {
         if (ht) u_th[q] = y_th[q] + dt / 2.0 * k[1][0][q] - 3.0 * dt / 2.0 * k[3][0][q] + 2.0 * dt * k[4][0][q];
         if (hp) u_ph[q] = y_ph[q] + dt / 2.0 * k[1][1][q] - 3.0 * dt / 2.0 * k[3][1][q] + 2.0 * dt * k[4][1][q];
@@ -312,14 +337,23 @@ void or_rkm_step(const or_model* m, const double* G, double t, double dt,
     or_rhs(m, G, t, ht ? u_th : NULL, hp ? u_ph : NULL, NULL, 0, k[5][0], k[5][1]);
 
     double E = 0.0;
-    for (long long q = 0; q < N; ++q) {
-        for (int f = 0; f < 2; ++f) {
-            if ((f == 0 && !ht) || (f == 1 && !hp)) continue;
-            const double* y = f == 0 ? y_th : y_ph;
-            double* o = f == 0 ? out_th : out_ph;
-            o[q] = y[q] + dt / 6.0 * (k[1][f][q] + 4.0 * k[4][f][q] + k[5][f][q]);
-            double e = fabs(dt / 30.0 * (2.0 * k[1][f][q] - 9.0 * k[3][f][q] + 8.0 * k[4][f][q] - k[5][f][q]));
-            if (!(e <= E)) E = e; /* a NaN propagates */
+#pragma omp parallel
+    {
+        double Et = 0.0; /* maximum over this thread's cells; once a NaN is seen it stays */
+#pragma omp for schedule(static)
+        for (long long q = 0; q < N; ++q) {
+            for (int f = 0; f < 2; ++f) {
+                if ((f == 0 && !ht) || (f == 1 && !hp)) continue;
+                const double* y = f == 0 ? y_th : y_ph;
+                double* o = f == 0 ? out_th : out_ph;
+                o[q] = y[q] + dt / 6.0 * (k[1][f][q] + 4.0 * k[4][f][q] + k[5][f][q]);
+                double e = fabs(dt / 30.0 * (2.0 * k[1][f][q] - 9.0 * k[3][f][q] + 8.0 * k[4][f][q] - k[5][f][q]));
+                if (Et == Et && !(e <= Et)) Et = e;
+            }
+        }
+#pragma omp critical
+        {
+            if (E == E && !(Et <= E)) E = Et;
         }
     }
     if (!ht && out_th && y_th) memcpy(out_th, y_th, (size_t)N * sizeof(double));

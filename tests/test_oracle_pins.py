@@ -590,3 +590,47 @@ def test_long_step_lands_exactly(oracle_mod):
         o = mk(oracle_mod, (1, 1, 1), 1e-6, "micro", xi=1e-6, alpha=1e9, t_freeze=tf)
         r = o.run(np.zeros(1), None, np.array([0.3]), 0.7, 100.0, 50.0, 1.0, 2, fixed=True, trace=True)
         assert r["trace"][1, 0] == tf
+
+
+# ------------------------------------------------------------------ threads and non-finite estimates
+def test_results_do_not_depend_on_thread_count(oracle_mod):
+    """The loops over cells may run on several threads: a Merson step, the glass field and an adaptive
+    run are bit-identical with one thread and with all of them."""
+    shape = (23, 17, 19)
+    h = 3e-4
+    o = mk(oracle_mod, shape, h, "full", alpha=4.17e6, xi=h, xi_G=0.4 * h, dirichlet_faces=I.FACE_ZP,
+           theta_freeze=-5.0)
+    sv, _ = I.packing_boolean(shape, 0.5, I.uniform_radius(3.0, 5.0), 5)
+    th0, ph0, _ = I.random_fields(shape, 9, theta_scale=2.0)
+    full = oracle_mod.threads()
+    out = []
+    try:
+        for n in (1, max(full, 2)):
+            oracle_mod.threads(n)
+            G = o.glass(sv * h, 0.4 * h)
+            th, ph, E = o.rkm_step(G, th0, ph0, 0.0, 0.01)
+            r = o.run(G, th0, ph0, 0.0, 0.01, 0.3, 1e-6, 100)
+            out.append((G, th, ph, E, r["theta"], r["phi"], r["n_accepted"], r["n_rejected"]))
+    finally:
+        oracle_mod.threads(full)
+    a, b = out
+    for x, y in zip(a, b):
+        assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def test_error_estimate_keeps_a_nan(oracle_mod):
+    """A NaN anywhere in the state makes the error estimate NaN (the run then stops as non-finite),
+    wherever the NaN sits in the visiting order and however many threads visit the cells."""
+    shape = (16, 4, 4)
+    o = mk(oracle_mod, shape, 1e-6, "micro", xi=1e-6, alpha=3e9, theta_micro=-0.5)
+    full = oracle_mod.threads()
+    try:
+        for n in (1, max(full, 2)):
+            oracle_mod.threads(n)
+            for pos in (0, 5, o.N - 1):
+                ph = np.full(o.N, 0.25)
+                ph[pos] = math.nan
+                _, _, E = o.rkm_step(np.zeros(o.N), None, ph, 0.0, 1e-9)
+                assert math.isnan(E), (n, pos)
+    finally:
+        oracle_mod.threads(full)
