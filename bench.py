@@ -144,68 +144,78 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def make_workload(n=N_SIDE):
+def make_workload(kind="full256", n=None):
+    """full256: the 256^3 bead packing (radii uniform in [10, 16] voxels); full512: the 512^3 packing
+    with lognormal radii (mean 12, log-sd 0.25), freeze then thaw.  n overrides the side (profiling)."""
+    if kind == "full512":
+        return I.lognormal_case(n or 512)
+    n = n or N_SIDE
     return I.full_bead_case(n, SEED, name=f"full_sigmap1p_{n}")
 
 
 class OracleCrop:
     """The oracle as it stands on a 128 x 128 x 32 crop at the top of the workload (Dirichlet face,
-    ice seed, beads), single thread.  Setup (the crop's glass field) is not timed."""
+    ice seed, beads).  Setup (the crop's glass field) is not timed."""
 
     SHAPE = (128, 128, 32)
 
     def __init__(self, w):
         import oracle
         oracle.build()
-        n = w.shape[0]
-        c = self.SHAPE
-        off = ((n - c[0]) // 2, (n - c[1]) // 2, n - c[2])
-        h = w.h
-        lo = np.array(off) * h
-        hi = (np.array(off) + np.array(c)) * h
-        sp = w.spheres
-        # spheres whose terms can reach the crop (beyond r + 40 xi_G they are below 1e-17)
-        reach = sp[:, 3] + 40 * w.params["xi_G"]
-        near = np.all((sp[:, :3] > lo - reach[:, None]) & (sp[:, :3] < hi + reach[:, None]), axis=1)
-        sps = sp[near].copy()
-        sps[:, :3] -= lo
-        self.o = oracle.Oracle(c, h, w.model, w.reaction, w.params)
-        self.G = self.o.glass(sps, w.params["xi_G"])
-        self.th = np.full(self.o.N, 1.0)
-        self.ph = I.top_slab_indicator(c, 2)
-        self.n_beads = len(sps)
-        self.cells = c[0] * c[1] * c[2]
+        self.oracle = oracle
+        c = I.top_crop(w, self.SHAPE, w.params["t_freeze"])
+        self.o = oracle.Oracle(c.shape, c.h, c.model, c.reaction, c.params)
+        self.G = self.o.glass(c.spheres, c.params["xi_G"])
+        self.th, self.ph = c.theta0, c.phi0
+        self.n_beads = c.extra["n_spheres"]
+        self.cells = int(np.prod(c.shape))
+        self.full = w.shape[0]
+
+    def threads(self, n=0):
+        return self.oracle.threads(n)
 
     def step(self):
         self.o.rkm_step(self.G, self.th, self.ph, 0.0, 0.01)
 
-    def describe(self, n, el):
+    def describe(self, n, el, threads):
         c = self.SHAPE
-        return (f"{n} Merson steps on a {c[0]}x{c[1]}x{c[2]} crop (top of the {N_SIDE}^3 workload, "
-                f"{self.n_beads} nearby beads), single thread, {el:.1f} s")
+        return (f"{n} Merson steps on a {c[0]}x{c[1]}x{c[2]} crop (top of the {self.full}^3 workload, "
+                f"{self.n_beads} nearby beads), {threads} thread{'s' if threads > 1 else ''}, {el:.1f} s")
 
 
-def cpu_sample(w, seconds=10.0, min_steps=2):
-    """cpu_baseline: the oracle timed for about `seconds` on the crop."""
-    oc = OracleCrop(w)
+def _time_oracle(oc, seconds, min_steps):
     n, t0 = 0, time.perf_counter()
     while True:
         oc.step()
         n += 1
         el = time.perf_counter() - t0
         if n >= min_steps and el >= seconds:
-            break
-    return {"value": oc.cells * 5 * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": oc.describe(n, el)}
+            return n, el
+
+
+def cpu_sample(w, seconds=10.0, min_steps=2):
+    """cpu_baseline: the oracle timed for about `seconds` on the crop with every host core (OpenMP over
+    the loops on cells), and again on one thread."""
+    oc = OracleCrop(w)
+    full = oc.threads()
+    n, el = _time_oracle(oc, seconds, min_steps)
+    out = {"value": oc.cells * 5 * n / el, "unit": UNIT, "cores": full, "kind": "oracle",
+           "sample": oc.describe(n, el, full)}
+    oc.threads(1)
+    n1, el1 = _time_oracle(oc, seconds, min_steps)
+    oc.threads(full)
+    out["single_thread"] = {"value": oc.cells * 5 * n1 / el1, "cores": 1, "sample": oc.describe(n1, el1, 1)}
+    return out
 
 
 def run_reference(args, rank, world):
-    """--impl reference: the oracle timed on the host cores (rank 0 only); one step = one
+    """--impl reference: the oracle timed on the host cores (rank 0 only, every core); one step = one
     oracle Merson step on the crop."""
     if rank != 0:
         return
-    w = make_workload()
+    w = make_workload(args.workload if args.workload in ("full256", "full512") else "full256")
     oc = OracleCrop(w)
+    cores = oc.threads()
     for _ in range(args.warmup):
         oc.step()
     t0 = time.perf_counter()
@@ -219,8 +229,8 @@ def run_reference(args, rank, world):
             "data": "synthetic", "config": {"workload": w.name, "grid": list(w.shape),
                                             "sample": "128x128x32 crop of the workload",
                                             "l2": "not applicable (CPU)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": oc.describe(args.steps, el)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": oc.describe(args.steps, el, cores)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -233,26 +243,67 @@ def set_tiles(g, tiles):
         g.autotune(None)
 
 
-def time_form(torch, pf, w, precision, steps, warmup, stream, tiles=None):
-    """Device-timed adaptive attempts of one precision form; returns timing and stage profile."""
-    g = pf.Grid(w.shape, w.h, w.model, w.reaction, precision, w.params, stream=stream)
-    g.set_geometry(w.spheres, w.x3_cap)
-    g.set_state(w.theta0, w.phi0, 0.0, 0.01)
-    set_tiles(g, tiles)
-    # warm-up attempts (also reaches the steady step size of the initial transient)
+def timed_window(torch, pf, g, state, steps, warmup, stream, barrier, clk=None):
+    """Adaptive attempts from `state` = (theta, phi): `warmup` untimed ones (they also reach the step
+    size of the state), then `steps` timed on the device with CUDA events on the grid's stream."""
+    g.set_state(state[0], state[1], 0.0, 0.01)
     g.run_to(math.inf, TOL, warmup)
-    torch.cuda.synchronize()
+    barrier()
     l0 = pf.pf_kernel_launches()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    if clk:
+        clk.__enter__()
+    t_wall = time.perf_counter()
     e0.record(stream)
     s = g.run_to(math.inf, TOL, steps)
     e1.record(stream)
     e1.synchronize()
-    ms = e0.elapsed_time(e1)
-    launches = pf.pf_kernel_launches() - l0
-    prof = g.profile_stages(3)
-    return g, s, ms, launches, prof
+    if clk:
+        clk.__exit__(None, None, None)
+    t_wall = time.perf_counter() - t_wall
+    barrier()
+    s["ms"] = e0.elapsed_time(e1)
+    s["launches"] = pf.pf_kernel_launches() - l0
+    s["wall_s"] = t_wall
+    s["attempts"] = s["n_accepted"] + s["n_rejected"]
+    return s
+
+
+def crop_study(pf, w, crop=128, t_freeze=10.0, t_end=20.0):
+    """Error of both precision forms against the binary64 oracle (all host cores) on the crop at the
+    top centre of the workload, through a freeze-then-thaw cycle: top face -5 K until t_freeze, +2 K
+    until t_end, tolerance 1e-6.  Compared at t_freeze (the most ice) and at t_end."""
+    import oracle
+    oracle.build()
+    c = I.top_crop(w, (crop, crop, crop), t_freeze)
+    o = oracle.Oracle(c.shape, c.h, c.model, c.reaction, c.params)
+    t0 = time.perf_counter()
+    G = o.glass(c.spheres, c.params["xi_G"])
+    legs = [o.run(G, c.theta0, c.phi0, 0.0, 0.01, t_freeze, TOL, 10 ** 6)]
+    legs.append(o.run(G, legs[0]["theta"], legs[0]["phi"], t_freeze, legs[0]["dt"], t_end, TOL, 10 ** 6))
+    oracle_s = time.perf_counter() - t0
+    ref_u = [o.uwc(G, r["phi"]) for r in legs]
+    out = {"crop": [crop] * 3, "beads": c.extra["n_spheres"], "t_freeze": t_freeze, "t_end": t_end,
+           "oracle_s": oracle_s, "oracle_threads": oracle.threads(),
+           "oracle": [{"attempts": [r["n_accepted"], r["n_rejected"]], "uwc": u["uwc"], "n_ice": u["n_ice"]}
+                      for r, u in zip(legs, ref_u)]}
+    for prec, key in ((I.PREC_FP64, "f64"), (I.PREC_FP32, "f32_fields")):
+        g = pf.Grid(c.shape, c.h, c.model, c.reaction, prec, c.params)
+        g.set_geometry(c.spheres)
+        g.set_state(c.theta0, c.phi0, 0.0, 0.01)
+        rows = []
+        for t_stop, ref, ru in zip((t_freeze, t_end), legs, ref_u):
+            st = g.run_to(t_stop, TOL, 10 ** 6)
+            th, ph, _, _ = g.get_state()
+            u = g.unfrozen_fraction()
+            rows.append({"attempts": [st["n_accepted"], st["n_rejected"]],
+                         "max_abs_dphi": float(np.max(np.abs(ph - ref["phi"]))),
+                         "max_abs_dtheta_K": float(np.max(np.abs(th - ref["theta"]))),
+                         "uwc": u["uwc"], "uwc_rel_err": abs(u["uwc"] - ru["uwc"]) / ru["uwc"]})
+        g.close()
+        out[key] = rows
+    return out
 
 
 def run_sweep(args, rank, world, dist):
@@ -569,9 +620,12 @@ def main():
     ap.add_argument("--no-fp32-form", action="store_true")
     ap.add_argument("--tiles", type=int, nargs=2, metavar=("BY", "ZC"), default=None,
                     help="fixed tile shape (block height, z chunk) instead of the autotuner's choice")
-    ap.add_argument("--workload", default="full256", choices=["full256", "sweep48", "warmstart", "macro", "uwc", "conv"],
-                    help="full256: the binary64 bead workload (default); sweep48: the 48-instance micro-scale "
+    ap.add_argument("--workload", default="full256",
+                    choices=["full256", "full512", "sweep48", "warmstart", "macro", "uwc", "conv"],
+                    help="full256: the binary64 bead workload (default); full512: the 512^3 lognormal packing, both "
+                         "forms, with the crop error study; sweep48: the 48-instance micro-scale "
                          "sweep, batched binary32 persistent run vs the plain binary64 method")
+    ap.add_argument("--no-crop-study", action="store_true", help="full512: skip the 128^3 crop error study")
     ap.add_argument("--max-steps", type=int, default=600, help="sweep48, uwc: attempt cap per instance")
     ap.add_argument("--macro-n3", type=int, default=100, help="macro: cells along the vessel height (100/200/400)")
     ap.add_argument("--macro-cap", type=int, default=1_500_000, help="macro: attempt cap per run")
@@ -584,7 +638,7 @@ def main():
     ap.add_argument("--train-steps", type=int, default=1500, help="warmstart: Adam steps")
     ap.add_argument("--test-side", type=int, default=256, help="warmstart: side of the inference grids")
     ap.add_argument("--tests", type=int, default=2, help="warmstart: number of inference instances")
-    ap.add_argument("--size", type=int, default=N_SIDE, help="grid side (256 = the benchmark workload; "
+    ap.add_argument("--size", type=int, default=None, help="grid side (default: the workload's; "
                     "smaller sizes are for profiling captures only)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -626,7 +680,7 @@ def main():
             dist.destroy_process_group()
         return
 
-    w = make_workload(args.size)
+    w = make_workload(args.workload, args.size)
     stream = torch.cuda.Stream()
     peaks, peak_kind = load_peaks()
 
@@ -635,34 +689,31 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---------------- timed region: binary64 adaptive attempts
+    # ---------------- binary64: the mid-front window (headline) and the window after t = 0
     g = pf.Grid(w.shape, w.h, w.model, w.reaction, I.PREC_FP64, w.params, stream=stream)
     g.set_geometry(w.spheres, w.x3_cap)
-    g.set_state(w.theta0, w.phi0, 0.0, 0.01)
+    G_host = g.get_glass()
+    mid = I.midfront_state(w, G_host)
+    t0_state = (w.theta0, w.phi0)
+    g.set_state(mid[0], mid[1], 0.0, 0.01)
     set_tiles(g, args.tiles)
     tiles = g.get_tiles()
-    g.run_to(math.inf, TOL, args.warmup)
-    barrier()
-    l0 = pf.pf_kernel_launches()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        t_wall = time.perf_counter()
-        e0.record(stream)
-        s = g.run_to(math.inf, TOL, args.steps)
-        e1.record(stream)
-        e1.synchronize()
-        t_wall = time.perf_counter() - t_wall
-    barrier()
-    ms = e0.elapsed_time(e1)
-    launches = pf.pf_kernel_launches() - l0
-    attempts = s["n_accepted"] + s["n_rejected"]
+    clk = ClockSampler(local)
+    s = timed_window(torch, pf, g, mid, args.steps, args.warmup, stream, barrier, clk)
+    prof = g.profile_stages(3)                        # dominant kernel, timed live on the grid's stream
+    s0 = timed_window(torch, pf, g, t0_state, args.steps, args.warmup, stream, barrier)
+    prof0 = g.profile_stages(3)
+    ms, launches, attempts, t_wall = s["ms"], s["launches"], s["attempts"], s["wall_s"]
     local_units = w.n_cells * 5 * attempts
     (ms_max,), (units,) = reduce_over_ranks(dist, [ms], [local_units], "cuda")
     value = units / (ms_max * 1e-3)
+    windows = {"midfront": {"value": value, "ms_per_step": ms / max(attempts, 1), "attempts": attempts,
+                            "accepted": s["n_accepted"]},
+               "t0": {"value": w.n_cells * 5 * s0["attempts"] / (s0["ms"] * 1e-3),
+                      "ms_per_step": s0["ms"] / max(s0["attempts"], 1), "attempts": s0["attempts"],
+                      "accepted": s0["n_accepted"],
+                      "stage_ms": dict(zip(["stage1", "stage2", "stage3", "stage4", "stage5", "controller"], prof0))}}
 
-    # ---------------- dominant kernel, timed live with CUDA events on the launching stream
-    prof = g.profile_stages(3)
     stage_names = ["stage1", "stage2", "stage3", "stage4", "stage5", "controller"]
     top = int(np.argmax(prof[:5]))
     top_ms = prof[top]
@@ -684,9 +735,8 @@ def main():
                 "stage_ms": dict(zip(stage_names, prof))}
 
     # ---------------- e2e: host-resident state in pinned memory, copies inside the timed region
-    pin_th = torch.from_numpy(w.theta0.copy()).pin_memory()
-    pin_ph = torch.from_numpy(w.phi0.copy()).pin_memory()
-    g.get_state(pin_th, pin_ph)
+    pin_th = torch.from_numpy(mid[0].copy()).pin_memory()
+    pin_ph = torch.from_numpy(mid[1].copy()).pin_memory()
     barrier()
     e2e_steps = max(3, args.steps // 2)
     t0 = time.perf_counter()
@@ -703,41 +753,59 @@ def main():
            "note": "per step: pf_set_state from pinned host theta/phi, one pf_run_to attempt, pf_unfrozen_fraction"}
     g.close()
 
-    # ---------------- binary32-field form on the same workload
+    # ---------------- binary32-field form on the same workload and windows
     forms = {}
     if not args.no_fp32_form:
-        g32, s32, ms32, l32, prof32 = time_form(torch, pf, w, I.PREC_FP32, args.steps, args.warmup, stream, args.tiles)
-        att32 = s32["n_accepted"] + s32["n_rejected"]
+        g32 = pf.Grid(w.shape, w.h, w.model, w.reaction, I.PREC_FP32, w.params, stream=stream)
+        g32.set_geometry(w.spheres, w.x3_cap)
+        g32.set_state(mid[0], mid[1], 0.0, 0.01)
+        set_tiles(g32, args.tiles)
+        s32 = timed_window(torch, pf, g32, mid, args.steps, args.warmup, stream, barrier)
+        prof32 = g32.profile_stages(3)
+        s32_0 = timed_window(torch, pf, g32, t0_state, args.steps, args.warmup, stream, barrier)
+        att32 = s32["attempts"]
         top32 = int(np.argmax(prof32[:5]))
         gbs32 = BYTES_F32[top32] * w.n_cells / (prof32[top32] * 1e-3) / 1e9
         forms["fp32_fields"] = {
-            "value": w.n_cells * 5 * att32 / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32 / max(att32, 1),
-            "gpu_launches": l32, "dtype": "f32 fields / f64 state", "tiles_by_zc": list(g32.get_tiles()),
+            "value": w.n_cells * 5 * att32 / (s32["ms"] * 1e-3), "unit": UNIT, "ms_per_step": s32["ms"] / max(att32, 1),
+            "window": "midfront",
+            "t0_value": w.n_cells * 5 * s32_0["attempts"] / (s32_0["ms"] * 1e-3),
+            "gpu_launches": s32["launches"], "dtype": "f32 fields / f64 state", "tiles_by_zc": list(g32.get_tiles()),
             "roofline": {"bound": "hbm", "kernel": f"merson_{stage_names[top32]}_full_sigmap1p_f32",
                          "achieved": gbs32, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": gbs32 / peaks["hbm_gbs"],
                          "step_gbs": sum(BYTES_F32) * w.n_cells / (sum(prof32[:5]) * 1e-3) / 1e9,
+                         "step_frac": sum(BYTES_F32) * w.n_cells / (sum(prof32[:5]) * 1e-3) / 1e9 / peaks["hbm_gbs"],
                          "traffic": None, "peak_source": peak_kind,
                          "stage_ms": dict(zip(stage_names, prof32))}}
         g32.close()
+
+    study = None
+    if rank == 0 and args.workload == "full512" and not args.no_crop_study:
+        study = crop_study(pf, w)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_sample(w)
 
     if rank == 0:
+        cfg = {"workload": w.name, "grid": list(w.shape), "h_m": w.h, "model": "full",
+               "reaction": "SigmaP1-P", "beads": int(w.extra["n_spheres"]),
+               "solid_fraction": round(w.extra["solid_fraction_sharp"], 4), "tol": TOL,
+               "window": "midfront: freezing front at half height (tanh profile in the pores), "
+                         f"{attempts} adaptive attempts after {args.warmup} warm-up attempts",
+               "attempts": attempts, "accepted": s["n_accepted"],
+               "l2": f"inputs larger than L2 (about {24 * 8 * w.n_cells / 1e9:.0f} GB working set)",
+               "tiles_by_zc": list(tiles),
+               "parallelism": "replicas" if world > 1 else "single GPU"}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / max(attempts, 1), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": w.name, "grid": list(w.shape), "h_m": w.h, "model": "full",
-                           "reaction": "SigmaP1-P", "beads": int(w.extra["n_spheres"]),
-                           "solid_fraction": round(w.extra["solid_fraction_sharp"], 4), "tol": TOL,
-                           "attempts": attempts, "accepted": s["n_accepted"],
-                           "l2": "inputs larger than L2 (about 2 GB working set)",
-                           "tiles_by_zc": list(tiles),
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "config": cfg, "windows": windows,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk.summary(), "forms": forms, "wall_s_timed": t_wall}
+        if study:
+            line["crop_error_study"] = study
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -294,6 +294,58 @@ def full_bead_case(n, seed, solid=0.60, r_lo=10.0, r_hi=16.0, radius_sampler=Non
                                          "n_spheres": len(sp)})
 
 
+def lognormal_case(n=512, seed=20240112, t_freeze=math.inf):
+    """Full-model freeze-then-thaw workload on an n^3 grid (512^3: about 14,600 beads): radii lognormal
+    with mean 12 voxels and log-standard deviation 0.25, Boolean placement to 60 % solid, h = 0.3 mm,
+    theta = +1 K, top face at -5 K until t_freeze and at +2 K after it (eq. BC-temperature-cap), ice seed
+    in the two top planes.  (A bead count of 40,000 at this mean radius would fill 2.2 times the box, so
+    the placement stops at the solid fraction instead.)"""
+    w = full_bead_case(n, seed, radius_sampler=lognormal_radius(12.0, 0.25), name=f"full_lognormal_{n}")
+    w.params["t_freeze"] = float(t_freeze)
+    return w
+
+
+def midfront_state(w, G, front=0.5, theta_cold=-5.0, theta_warm=1.0):
+    """A state of a bead workload (top face cold) with its freezing front at the fraction `front` of the
+    height: phi = 1/2 (1 + tanh((z - z_f) / (2 xi))) in the pore cells (G < 1/2; the planar interface
+    profile of the Allen-Cahn equation, Sec. 2.2) and 0 in the glass; theta rising linearly from 0 at
+    the front to theta_cold at the top face, and from 0 at the front to theta_warm 20 cells below it.
+    Used to time the stage kernels on the mix of cells a run meets half way, without running there."""
+    n1, n2, n3 = w.shape
+    xi = w.params["xi"]
+    z = (np.arange(n3) + 0.5) * w.h
+    L = n3 * w.h
+    zf = front * L
+    prof = 0.5 * (1.0 + np.tanh((z - zf) / (2.0 * xi)))
+    th_z = np.where(z >= zf, theta_cold * (z - zf) / (L - zf), theta_warm * np.minimum(1.0, (zf - z) / (20 * w.h)))
+    G3 = np.asarray(G).reshape(n3, n2, n1)
+    phi = np.where(G3 < 0.5, prof[:, None, None], 0.0)
+    theta = np.broadcast_to(th_z[:, None, None], (n3, n2, n1))
+    return np.ascontiguousarray(theta, dtype=np.float64).ravel(), np.ascontiguousarray(phi, dtype=np.float64).ravel()
+
+
+def top_crop(w, crop, t_freeze, name=None):
+    """The crop x [off, off + crop) of a bead workload at the top centre of its box, as a problem of its
+    own: the beads whose glass terms reach the crop (beyond r + 40 xi_G they are below 1e-17), shifted;
+    the same top face (Dirichlet, freeze then thaw at t_freeze) and seed planes; the cut faces insulated."""
+    n1, n2, n3 = w.shape
+    c1, c2, c3 = crop
+    off = np.array([(n1 - c1) // 2, (n2 - c2) // 2, n3 - c3], dtype=np.float64)
+    lo = off * w.h
+    hi = (off + np.array(crop, dtype=np.float64)) * w.h
+    sp = w.spheres
+    reach = sp[:, 3] + 40 * w.params["xi_G"]
+    near = np.all((sp[:, :3] > lo - reach[:, None]) & (sp[:, :3] < hi + reach[:, None]), axis=1)
+    sps = sp[near].copy()
+    sps[:, :3] -= lo
+    p = dict(w.params)
+    p["t_freeze"] = float(t_freeze)
+    ncell = c1 * c2 * c3
+    return Workload(name or f"{w.name}_crop{c1}", tuple(crop), w.h, w.model, w.reaction, p, sps, w.x3_cap,
+                    np.full(ncell, float(w.theta0[0])), top_slab_indicator(tuple(crop), 2),
+                    extra={"offset_vox": off.astype(int).tolist(), "n_spheres": len(sps)})
+
+
 # Surface-tension scales and supercoolings of the micro-scale parametric sweep.
 SIGMA_SCALES = (1.0, 3.0, 10.0, 30.0, 100.0, 300.0)
 SUPERCOOLINGS = (0.1, 0.2, 0.5, 1.0, 2.0, 5.0, 10.0, 20.0)

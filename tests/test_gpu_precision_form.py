@@ -108,6 +108,66 @@ def test_fp32_form_freeze_thaw_against_oracle(env):
     assert duwc <= 5e-3
 
 
+# The 512^3 lognormal freeze-then-thaw workload's error study: its 128^3 crop at the top centre of the
+# box (the beads that reach it, the cold face, the seed), top face at -5 K for T_FREEZE seconds and at
+# +2 K until T_END, adaptive tolerance 1e-6; the oracle runs on all host cores.
+CROP, T_FREEZE, T_END = 128, 10.0, 20.0
+
+
+@pytest.fixture(scope="module")
+def lognormal_crop(env):
+    torch, pf, oracle = env
+    w = I.lognormal_case(512)
+    c = I.top_crop(w, (CROP, CROP, CROP), T_FREEZE)
+    o = oracle.Oracle(c.shape, c.h, c.model, c.reaction, c.params)
+    G = o.glass(c.spheres, c.params["xi_G"])
+    legs = []
+    r = o.run(G, c.theta0, c.phi0, 0.0, 0.01, T_FREEZE, 1e-6, 200000)
+    assert r["status"] == 0 and r["t"] == T_FREEZE
+    legs.append(r)
+    r = o.run(G, r["theta"], r["phi"], r["t"], r["dt"], T_END, 1e-6, 200000)
+    assert r["status"] == 0 and r["t"] == T_END
+    legs.append(r)
+    return c, o, G, legs
+
+
+def test_lognormal_crop_freeze_thaw_both_forms(env, lognormal_crop):
+    """Both precision forms through the freeze-then-thaw cycle of the 128^3 crop, against the binary64
+    oracle at the end of the freezing leg (the most ice) and at the end of the cycle: binary64 takes the
+    oracle's accepted/rejected steps on both legs; the binary32-field form stays within max|dphi| <= 1e-3
+    and unfrozen-water fraction within 0.5 % relative."""
+    torch, pf, oracle = env
+    c, o, G, legs = lognormal_crop
+    ref_u = [o.uwc(G, r["phi"]) for r in legs]
+    # the cycle freezes a measurable amount and thaws part of it back
+    assert ref_u[0]["n_ice"] > 10000 and ref_u[1]["n_ice"] < ref_u[0]["n_ice"]
+    report = []
+    for prec in (I.PREC_FP64, I.PREC_FP32):
+        g = pf.Grid(c.shape, c.h, c.model, c.reaction, prec, c.params)
+        g.set_geometry(c.spheres)
+        g.set_state(c.theta0, c.phi0, 0.0, 0.01)
+        for leg, (t_stop, ref, ru) in enumerate(zip((T_FREEZE, T_END), legs, ref_u)):
+            s = g.run_to(t_stop, 1e-6, 200000)
+            th, ph, t, _ = g.get_state()
+            u = g.unfrozen_fraction()
+            assert t == t_stop
+            dphi = float(np.max(np.abs(ph - ref["phi"])))
+            dth = float(np.max(np.abs(th - ref["theta"])))
+            duwc = abs(u["uwc"] - ru["uwc"]) / ru["uwc"]
+            report.append(f"{'f64' if prec == I.PREC_FP64 else 'f32'} leg {leg}: steps {s['n_accepted']}/{s['n_rejected']} "
+                          f"(oracle {ref['n_accepted']}/{ref['n_rejected']}), max|dphi| {dphi:.2e}, "
+                          f"max|dtheta| {dth:.2e} K, uwc {u['uwc']:.6f} (oracle {ru['uwc']:.6f}, rel {duwc:.1e})")
+            if prec == I.PREC_FP64:
+                assert (s["n_accepted"], s["n_rejected"]) == (ref["n_accepted"], ref["n_rejected"])
+                assert rel(ph, ref["phi"]) <= 1e-8 and rel(th, ref["theta"]) <= 1e-8
+                assert (u["n_ice"], u["n_water"]) == (ru["n_ice"], ru["n_water"])
+            else:
+                assert dphi <= 1e-3
+                assert duwc <= 5e-3
+        g.close()
+    print("\n" + "\n".join(report))
+
+
 @pytest.mark.slow
 def test_fp32_form_full_size_fixed_steps_256(env):
     """256^3 full model (the benchmark size) in the autotuned launch configuration the bench times:
