@@ -180,9 +180,12 @@ pf_status pf_autotune(pf_grid* g, const char* cache_path, int* by, int* zc, doub
 
 /* ---- Batched persistent runs (independent instances, each with its own adaptive step).
  * Equilibrium test (Sec. 3.3: the unfrozen water content no longer changes): stage 1 counts the ice
- * cells of the pore bulk, #{phi > 1/2 and I_W(G) > 1/2}, of the current state; an instance is in
- * equilibrium at the first state whose count has stayed within eq_rel_tol x (pore-bulk cells) of a
- * reference value for eq_window seconds (eq_rel_tol = 0: no change at all).  (The thin glass
+ * cells of the pore bulk, #{phi > 1/2 and I_W(G) > 1/2}, of the current state and takes the largest
+ * |dphi/dt| over those pore-bulk cells; an instance is in equilibrium at the first state whose count has
+ * stayed within eq_rel_tol x (pore-bulk cells) of a reference value for eq_window seconds
+ * (eq_rel_tol = 0: no change at all) and, when eq_rate is given and eq_rate[i] > 0, whose largest
+ * |dphi/dt| is at most eq_rate[i] (a residual test: 4 xi |dphi/dt| is the speed of a tanh interface,
+ * Sec. 2.2, so eq_rate = v / (4 xi) bounds the speed of every pore interface by v).  (The thin glass
  * layer with I_W -> 0 keeps relaxing on the slow time scale alpha xi^2 / I_W without moving any pore
  * interface; it is left out of the test but not out of pf_unfrozen_fraction.)
  * A batch takes ownership of n grids (1 <= n <= 256) that share model, reaction and precision but may
@@ -198,6 +201,7 @@ typedef struct pf_batch pf_batch;
 typedef struct pf_batch_result {
     pf_run_stats stats;
     double t_eq;       /* time at which the equilibrium test held (NaN if it did not) */
+    double rate;       /* largest |dphi/dt| over the pore-bulk cells at the last attempt */
     int equilibrium;   /* 1 if the run stopped on the equilibrium test */
     int status;        /* PF_OK, PF_E_DT_UNDERFLOW or PF_E_NONFINITE for this instance */
 } pf_batch_result;
@@ -206,11 +210,40 @@ pf_status pf_batch_destroy(pf_batch* b);
 pf_grid* pf_batch_grid(pf_batch* b, int i);
 /* One block height for all instances (minimising the summed best times), then the best zc per instance. */
 pf_status pf_batch_autotune(pf_batch* b, const char* cache_path);
-pf_status pf_batch_run_to(pf_batch* b, const double* t_end, const double* eq_window, double eq_rel_tol, double tol,
-                          long long max_steps, pf_batch_result* res);
+pf_status pf_batch_run_to(pf_batch* b, const double* t_end, const double* eq_window, double eq_rel_tol,
+                          const double* eq_rate, double tol, long long max_steps, pf_batch_result* res);
 /* Device-side loop iterations of the last pf_batch_run_to (steps of the slowest instance + 1). */
 long long pf_batch_iterations(const pf_batch* b);
 const char* pf_batch_last_error(const pf_batch* b);
+
+/* ---- z-slab multi-domain mode (Sec. 2.5: the domain cut along x3 into slabs; the planes next to a cut
+ * are exchanged between neighbour slabs before every stage that reads them, and the step control uses
+ * the error maximum over all slabs).  Here all slabs live in one process on one GPU: each slab is a grid
+ * with a ghost plane at every cut, the exchange is a copy kernel after each stage (and after setting the
+ * state), and the slabs share one device-side control block, so the error maximum and the pore counts
+ * accumulate over all slabs and one step controller decides.  Results are bit-identical to the
+ * single-domain grid of the same size: every cell sees the same neighbour values and arithmetic.
+ *   nslabs : 1 <= nslabs <= min(n3, 1024);
+ *   planes : nslabs + 1 increasing plane indices from 0 to n3 (slab q holds planes [planes[q],
+ *            planes[q+1])), or NULL for an even split;
+ *   other arguments as pf_create_grid; Dirichlet z faces apply only at the two ends of the domain.
+ * Host arrays of set_state / get_state hold the whole n1 x n2 x n3 grid.  pf_slabs_grid returns slab q's
+ * grid (owned by the group; use it only for reads such as pf_get_glass).  pf_slabs_halo_bytes: bytes the
+ * exchanges of the last pf_slabs_run_to moved.  Errors as for the single-grid calls; messages from
+ * pf_slabs_last_error. */
+typedef struct pf_slabs pf_slabs;
+pf_status pf_slabs_create(int n1, int n2, int n3, double h, int model, int reaction, int precision,
+                          const pf_params* p, int nslabs, const int* planes, void* stream, pf_slabs** out);
+pf_status pf_slabs_destroy(pf_slabs* s);
+pf_grid* pf_slabs_grid(pf_slabs* s, int q);
+pf_status pf_slabs_set_geometry(pf_slabs* s, const double* spheres, long long n, double x3_cap);
+pf_status pf_slabs_set_tiles(pf_slabs* s, int by, int zc);
+pf_status pf_slabs_set_state(pf_slabs* s, const double* theta, const double* phi, double t, double dt);
+pf_status pf_slabs_get_state(pf_slabs* s, double* theta, double* phi, double* t, double* dt);
+pf_status pf_slabs_run_to(pf_slabs* s, double t_end, double tol, long long max_steps, pf_run_stats* stats);
+pf_status pf_slabs_unfrozen_fraction(pf_slabs* s, double* uwc, long long* n_ice, long long* n_water);
+long long pf_slabs_halo_bytes(const pf_slabs* s);
+const char* pf_slabs_last_error(const pf_slabs* s);
 
 /* Throughput probes of the current device: binary64 and binary32 FMA rates (TFLOP/s, FMA = 2 flops,
  * 8 independent chains per thread, 8 blocks of 256 threads per SM) and device-memory copy bandwidth

@@ -94,6 +94,64 @@ pf_status pfnn_pack_input(const float* G, const float* feat, int nfeat, long lon
 pf_status pfnn_adam(float* p, const float* g, float* m, float* v, void* p_bf16, long long n, float lr, float b1,
                     float b2, float eps, int step, void* stream);
 
+/* Warm-start constraint (the micro-scale model of Sec. 2.4 has no nucleation term: ice only exists where
+ * it grew from the seed through the pore space).  From the network output prob (device fp32, n1 n2 n3,
+ * x fastest), the seed phase field phi_seed and the glass field G (device binary64): the cells that may
+ * carry ice are those with prob > 1/2 and a water indicator 1 - zeta G above zero; the ones connected to
+ * the seed (phi_seed > 1/2) through face neighbours, grown by `halo` cells (0..64) to keep the diffuse
+ * interface, take max(prob clamped to [0, 1], phi_seed); every other cell takes phi_seed (cells with a zero water
+ * indicator never change).  work: caller-owned device scratch of at least 16 * ceil(n / 16) + 4 bytes.
+ * The flood fill sweeps in place until a sweep reaches no new cell (checked every 16 sweeps; bounded by
+ * the cell count); *sweeps (may be NULL) receives the sweeps run.  Synchronises `stream`. */
+pf_status pfnn_seed_connect(const float* prob, const double* phi_seed, const double* G, int n1, int n2, int n3,
+                            double zeta, int halo, unsigned char* work, double* phi_out, void* stream,
+                            long long* sweeps);
+
+/* ---- The warm-start network as one object (pfnn_net): the 3D convolutional encoder-decoder of 4 levels
+ * (16/32/64/128 channels; two 3x3x3 convolutions + ReLU per level, 2x2x2 average pooling down, x2 nearest
+ * upsampling + 3x3x3 convolution up, skip concatenation, 1x1x1 sigmoid head) that predicts the micro-scale
+ * equilibrium phase field from the glass field and two features (supercooling, surface-tension scale).
+ * The library owns the FP32 master weights, their BF16 working copies, the gradients, the Adam moments and
+ * the activation buffers (allocated with cudaMalloc at creation and on the first forward of a new batch
+ * shape); forward, backward and the Adam step are sequences of the kernels above on the net's stream.
+ * Parameters are numbered 0 .. pfnn_net_params() - 1 in forward order (the last is the head);
+ * convolution weights are [27][cout][cin], the head's [16] with one bias.
+ *   create  : He-normal weights (std sqrt(2 / (27 cin)); the head sqrt(1/16)) from a splitmix64/Box-Muller
+ *             stream seeded by `seed`, zero biases; stream = cudaStream_t (NULL = legacy default stream).
+ *   forward : G fp32 [n][side^3] (glass field, x fastest), feat fp32 [n][2], DEVICE pointers; side a
+ *             multiple of 8, >= 8; prob (device, n side^3 fp32) receives the sigmoid output.  With a target
+ *             (device fp32, NULL = none) it also forms the mean binary cross-entropy (pfnn_net_loss) and
+ *             keeps what pfnn_net_backward needs.  pfnn_net_infer = forward without a target.
+ *   backward: gradients of that loss into every parameter (PF_E_STATE without a forward with a target).
+ *   set/get : host arrays, synchronous.  Errors: PF_E_INVALID, PF_E_OOM, PF_E_CUDA, PF_E_STATE; the failing
+ *             step is named by pfnn_net_last_error. */
+typedef struct pfnn_net pfnn_net;
+int pfnn_net_params(void);
+const char* pfnn_net_param_name(int q);
+pf_status pfnn_net_param_shape(int q, int* cin, int* cout);
+pf_status pfnn_net_create(unsigned long long seed, void* stream, pfnn_net** out);
+pf_status pfnn_net_destroy(pfnn_net* net);
+pf_status pfnn_net_set_params(pfnn_net* net, int q, const float* w, const float* b);
+pf_status pfnn_net_get_params(pfnn_net* net, int q, float* w, float* b);
+pf_status pfnn_net_get_grads(pfnn_net* net, int q, float* gw, float* gb);
+pf_status pfnn_net_forward(pfnn_net* net, const float* G, const float* feat, int n, int side, const float* target,
+                           float* prob);
+pf_status pfnn_net_infer(pfnn_net* net, const float* G, const float* feat, int n, int side, float* prob);
+pf_status pfnn_net_loss(pfnn_net* net, double* loss);
+pf_status pfnn_net_backward(pfnn_net* net);
+pf_status pfnn_net_adam_step(pfnn_net* net, float lr, float b1, float b2, float eps);
+const char* pfnn_net_last_error(const pfnn_net* net);
+/* Inspection of the wiring and of the buffers of the last forward / backward: pfnn_net_layer fills
+ * wiring[12] = {input buffer, input channel offset, cin, output buffer, output offset, cout, level, pre (0
+ * none, 1 pooling, 2 upsampling), pre input buffer, pre channels, pre output buffer, pre level} for
+ * convolution q < pfnn_net_params() - 1; buffer b (0 <= b < pfnn_net_buffers()) holds bf16 activations and
+ * fp32 gradients with `channels` per voxel at side >> level; pfnn_net_read_buffer copies them to host
+ * arrays of n (side >> level)^3 channels values (PF_E_STATE before the first forward). */
+int pfnn_net_buffers(void);
+pf_status pfnn_net_layer(int q, int* wiring);
+pf_status pfnn_net_buffer(int b, int* channels, int* level);
+pf_status pfnn_net_read_buffer(pfnn_net* net, int b, void* act_bf16, float* grad);
+
 #ifdef __cplusplus
 }
 #endif

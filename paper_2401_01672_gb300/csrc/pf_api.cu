@@ -24,6 +24,11 @@ static thread_local std::string t_create_err;
 struct pf_grid {
     int n1 = 0, n2 = 0, n3 = 0;
     long long N = 0;
+    // z-slab of a multi-domain group: ghost planes below / above (filled by the neighbour slab),
+    // global index of local plane 0, cells allocated per ghosted array (N plus the ghost planes)
+    int zg_lo = 0, zg_hi = 0, k_off = 0;
+    long long NA = 0;
+    bool own_ctrl = true;
     double h = 0;
     int model = 0, rx = 0, prec = 0;
     pf_params p{};
@@ -42,7 +47,7 @@ struct pf_grid {
     void* k4_th = nullptr; void* k4_ph = nullptr;
     double* G64 = nullptr;
     float* G32 = nullptr;
-    double* statics = nullptr;  // full model, binary64: 8 per-cell coefficient arrays (see StageArgs)
+    double* statics = nullptr;  // full model, binary64: NSTATIC per-cell coefficient arrays (see StageArgs)
     double* scratch64 = nullptr;
     void* red = nullptr;
     size_t red_bytes = 0;
@@ -96,20 +101,22 @@ __global__ void k_to_f32(const double* __restrict__ in, float* __restrict__ out,
 
 // Sec. 2.1, G_balls: one block per sphere scatters 1/2 (1 - tanh((|x - x_s| - r_s)/(2 xi_G))) into the
 // cells within r_s + 40 xi_G of its centre by atomicMax on the bit pattern (G >= 0).  Beyond that radius
-// the term is below e^-40 and is skipped.
+// the term is below e^-40 and is skipped.  The array holds global planes kofs .. kofs + n3 - 1 (a z-slab
+// with its ghost planes; kofs = 0 for a whole grid); cell centres use the global indices.
 __global__ void k_glass_spheres(const double* __restrict__ sp, long long ns, double* G, int n1, int n2, int n3,
-                                double h, double xi_G) {
+                                int kofs, double h, double xi_G) {
     const long long s = blockIdx.x;
     if (s >= ns) return;
     const double cx = sp[4 * s], cy = sp[4 * s + 1], cz = sp[4 * s + 2], r = sp[4 * s + 3];
     const double rc = r + 40.0 * xi_G;
     int lo[3], hi[3];
     const double cc[3] = {cx, cy, cz};
-    const int nn[3] = {n1, n2, n3};
+    const int nlo[3] = {0, 0, kofs};
+    const int nhi[3] = {n1 - 1, n2 - 1, kofs + n3 - 1};
     for (int d = 0; d < 3; ++d) {
         double a = floor((cc[d] - rc) / h - 0.5), b = ceil((cc[d] + rc) / h - 0.5);
-        lo[d] = (int)fmax(0.0, a);
-        hi[d] = (int)fmin((double)(nn[d] - 1), b);
+        lo[d] = (int)fmax((double)nlo[d], a);
+        hi[d] = (int)fmin((double)nhi[d], b);
     }
     if (lo[0] > hi[0] || lo[1] > hi[1] || lo[2] > hi[2]) return;
     const long long bx = hi[0] - lo[0] + 1, byy = hi[1] - lo[1] + 1, bz = hi[2] - lo[2] + 1;
@@ -124,15 +131,16 @@ __global__ void k_glass_spheres(const double* __restrict__ sp, long long ns, dou
         const double dist = sqrt(dx * dx + dy * dy + dz * dz);
         if (dist - r > 40.0 * xi_G) continue;
         const double g = 0.5 * (1.0 - tanh((dist - r) * inv2x));
-        if (g > 0.0) atomicMax(&Gb[i + (long long)n1 * (j + (long long)n2 * k)], (unsigned long long)__double_as_longlong(g));
+        if (g > 0.0)
+            atomicMax(&Gb[i + (long long)n1 * (j + (long long)n2 * (k - kofs))], (unsigned long long)__double_as_longlong(g));
     }
 }
 
-// Sec. 2.1: G = max(G_balls, 1/2 (1 + tanh((x3 - x3cap)/(2 xi_G))))
-__global__ void k_glass_cap(double* G, int n1, int n2, int n3, double h, double xi_G, double x3cap) {
+// Sec. 2.1: G = max(G_balls, 1/2 (1 + tanh((x3 - x3cap)/(2 xi_G))))  (array plane 0 = global plane kofs)
+__global__ void k_glass_cap(double* G, int n1, int n2, int n3, int kofs, double h, double xi_G, double x3cap) {
     const long long n = (long long)n1 * n2 * n3;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(q / ((long long)n1 * n2));
+        const int k = (int)(q / ((long long)n1 * n2)) + kofs;
         const double z = (k + 0.5) * h;
         const double g = 0.5 * (1.0 + tanh((z - x3cap) / (2.0 * xi_G)));
         if (g > G[q]) G[q] = g;
@@ -142,7 +150,9 @@ __global__ void k_glass_cap(double* G, int n1, int n2, int n3, double h, double 
 // Per-cell coefficients of the full model from G (eq. material-properties-blending-formula): with
 // w(phi) = A_w + B_w phi, A_w = w_L + G (w_G - w_L), B_w = (1 - G)(w_I - w_L):
 //   lambda' = A_lam + B_lam phi (scaled by 1/(2h^2)), W = 2 (1 - zeta G)/(alpha xi^2),
-//   rho c = A_rho A_c + (A_rho B_c + B_rho A_c) phi + B_rho B_c phi^2,  rho L = L A_rho + L B_rho phi.
+//   rho c = A_rho A_c + (A_rho B_c + B_rho A_c) phi + B_rho B_c phi^2,  rho L = L A_rho + L B_rho phi,
+//   and 1/(rho c) at phi = 0 and at phi = 1 (IEEE division), used where phi and its six neighbours
+//   are all exactly 0 or all exactly 1 (there dphi/dt = 0 and dtheta/dt = div / (rho c)).
 __global__ void k_full_statics(const double* __restrict__ G, double* __restrict__ S, long long n, CoefT<double> k) {
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
         const double g = G[q];
@@ -156,6 +166,10 @@ __global__ void k_full_statics(const double* __restrict__ G, double* __restrict_
         S[5 * n + q] = br * bc;
         S[6 * n + q] = k.latent * ar;
         S[7 * n + q] = k.latent * br;
+        const double c0 = ar * ac;
+        const double c1 = c0 + fma(ar, bc, br * ac) + br * bc;
+        S[8 * n + q] = 1.0 / c0;
+        S[9 * n + q] = 1.0 / c1;
     }
 }
 
@@ -173,21 +187,25 @@ __global__ void k_temp_phi(const double* __restrict__ th, const double* __restri
 // dt * min(5, 0.8 (tol/E)^(1/5)) capped at dt_max; the next step is shortened to land on t_freeze or
 // t_end.  With eq_window > 0 the run stops, before accepting, once the pore-bulk ice count of the
 // current state (measured in stage 1) has stayed within eq_rel_tol x (pore-bulk cells) of a reference
-// value for eq_window seconds (the state is then the one at t_eq = t).
+// value for eq_window seconds and, when eq_rate > 0, the largest |dphi/dt| over the pore-bulk cells of
+// that state is at most eq_rate (the state is then the one at t_eq = t).
 __device__ void controller_step(Ctrl* c) {
     if (c->done) return;
     const double E = __longlong_as_double((long long)c->err_bits);
     const long long cnt = (long long)c->ice_count;
     const double tolc = c->eq_rel_tol * (double)c->pore_count;
+    const double rate = __longlong_as_double((long long)c->rate_bits);
     c->err_bits = 0ULL;
     c->ice_count = 0ULL;
     c->pore_count = 0ULL;
+    c->rate_bits = 0ULL;
     c->last_err = E;
+    c->last_rate = rate;
     if (c->eq_window > 0.0) {
         if (c->prev_count < 0 || fabs((double)(cnt - c->prev_count)) > tolc) {
             c->prev_count = cnt;
             c->last_change_t = c->t;
-        } else if (c->t - c->last_change_t >= c->eq_window) {
+        } else if (c->t - c->last_change_t >= c->eq_window && (c->eq_rate <= 0.0 || rate <= c->eq_rate)) {
             c->equilibrium = 1;
             c->t_eq = c->t;
             c->accepted = 0;
@@ -424,7 +442,7 @@ static StageArgs<T> make_args(pf_grid* g) {
     else a.G = g->G64;
     a.zc = g->zc;
     a.statics = g->statics;
-    a.ncell = g->N;
+    a.ncell = g->NA;
     return a;
 }
 
@@ -511,8 +529,15 @@ pf_status pf_destroy_grid(pf_grid* g) {
     return PF_OK;
 }
 
-pf_status pf_create_grid(int n1, int n2, int n3, double h, int model, int reaction, int precision,
-                         const pf_params* p, void* stream, pf_grid** out) {
+// Options of a grid that is one z-slab of a multi-domain group (all zero for a whole grid).
+struct SlabOpts {
+    int zg_lo = 0, zg_hi = 0;  // ghost plane below / above
+    int k_off = 0;             // global index of local plane 0
+    pf_grid* ctrl_owner = nullptr;  // shares this grid's control block (step control of the group)
+};
+
+static pf_status create_impl(int n1, int n2, int n3, double h, int model, int reaction, int precision,
+                             const pf_params* p, void* stream, const SlabOpts& so, pf_grid** out) {
     if (!out) return fail(nullptr, PF_E_INVALID, "out is NULL");
     *out = nullptr;
     if (!p) return fail(nullptr, PF_E_INVALID, "params is NULL");
@@ -533,13 +558,21 @@ pf_status pf_create_grid(int n1, int n2, int n3, double h, int model, int reacti
     pf_grid* g = new pf_grid();
     g->n1 = n1; g->n2 = n2; g->n3 = n3;
     g->N = (long long)n1 * n2 * n3;
+    g->zg_lo = so.zg_lo; g->zg_hi = so.zg_hi; g->k_off = so.k_off;
+    const long long plane = (long long)n1 * n2;
+    g->NA = g->N + (long long)(so.zg_lo + so.zg_hi) * plane;
     g->h = h;
     g->model = model; g->rx = reaction; g->prec = precision;
     g->p = *p;
     g->stream = (cudaStream_t)stream;
     Coefs& c = g->cf;
     c.n1 = n1; c.n2 = n2; c.n3 = n3;
+    c.zlo = so.zg_lo ? -1 : 0;
+    c.zhi = so.zg_hi ? n3 : n3 - 1;
     c.dirichlet = (model == PF_MODEL_MICRO) ? 0 : (p->dirichlet_faces & 63);
+    // a face shared with a neighbour slab is interior to the domain: no boundary condition there
+    if (so.zg_lo) c.dirichlet &= ~PF_FACE_ZM;
+    if (so.zg_hi) c.dirichlet &= ~PF_FACE_ZP;
     c.harmonic = p->harmonic_mean ? 1 : 0;
     c.theta_freeze = p->theta_freeze; c.theta_thaw = p->theta_thaw; c.t_freeze = p->t_freeze;
     fill_coefs(g->k64, *p, h);
@@ -553,21 +586,36 @@ pf_status pf_create_grid(int n1, int n2, int n3, double h, int model, int reacti
     const size_t nd = sizeof(double) * g->N, nf = fbytes(g) * g->N;
     bool ok = true;
     auto A = [&](size_t b) { void* q = alloc(b); ok = ok && q; return q; };
+    // arrays read at the z neighbours get the ghost planes; the pointer kept is that of local plane 0
+    auto AG = [&](size_t esz) -> void* {
+        char* q = (char*)alloc(esz * (size_t)g->NA);
+        ok = ok && q;
+        return q ? q + esz * (size_t)(so.zg_lo * plane) : nullptr;
+    };
     if (has_th(g)) {
-        g->y_th[0] = (double*)A(nd); g->y_th[1] = (double*)A(nd);
-        g->ua_th = A(nf); g->ub_th = A(nf); g->k1_th = A(nf); g->k3_th = A(nf); g->k4_th = A(nf);
+        g->y_th[0] = (double*)AG(8); g->y_th[1] = (double*)AG(8);
+        g->ua_th = AG(fbytes(g)); g->ub_th = AG(fbytes(g)); g->k1_th = A(nf); g->k3_th = A(nf); g->k4_th = A(nf);
     }
     if (has_ph(g)) {
-        g->y_ph[0] = (double*)A(nd); g->y_ph[1] = (double*)A(nd);
-        g->ua_ph = A(nf); g->ub_ph = A(nf); g->k1_ph = A(nf); g->k3_ph = A(nf); g->k4_ph = A(nf);
+        g->y_ph[0] = (double*)AG(8); g->y_ph[1] = (double*)AG(8);
+        g->ua_ph = AG(fbytes(g)); g->ub_ph = AG(fbytes(g)); g->k1_ph = A(nf); g->k3_ph = A(nf); g->k4_ph = A(nf);
     }
-    g->G64 = (double*)A(nd);
-    if (is_f32(g)) g->G32 = (float*)A(sizeof(float) * g->N);
-    if (!is_f32(g) && model == PF_MODEL_FULL) g->statics = (double*)A(8 * nd);
+    g->G64 = (double*)AG(8);
+    if (is_f32(g)) g->G32 = (float*)AG(4);
+    if (!is_f32(g) && model == PF_MODEL_FULL) {
+        // NSTATIC arrays of NA cells each, ghost planes included (stride NA between arrays)
+        char* q = (char*)A(NSTATIC * sizeof(double) * (size_t)g->NA);
+        g->statics = q ? (double*)(q + sizeof(double) * (size_t)(so.zg_lo * plane)) : nullptr;
+    }
     g->scratch64 = (double*)A(nd);
     g->red_bytes = sizeof(UwcPart) * (152 * 16 + 2);
     g->red = A(g->red_bytes);
-    g->dctrl = (Ctrl*)A(sizeof(Ctrl));
+    if (so.ctrl_owner) {
+        g->own_ctrl = false;
+        g->dctrl = so.ctrl_owner->dctrl;
+    } else {
+        g->dctrl = (Ctrl*)A(sizeof(Ctrl));
+    }
     g->ptab = (double**)A(4 * sizeof(double*));
     cudaGetLastError();
     if (!ok) {
@@ -584,15 +632,17 @@ pf_status pf_create_grid(int n1, int n2, int n3, double h, int model, int reacti
         destroy_impl(g);
         return fail(nullptr, PF_E_CUDA, "stream creation failed");
     }
-    // default state: all water, theta = 0, phi = 0, t = 0
+    // default state: all water, theta = 0, phi = 0, t = 0 (ghost planes included)
+    const size_t gbytes = sizeof(double) * (size_t)(so.zg_lo * plane);
     double* h_tab[4] = {g->y_ph[0], g->y_ph[1], g->y_th[0], g->y_th[1]};
     cudaError_t e = cudaMemcpy(g->ptab, h_tab, sizeof(h_tab), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->dctrl, 0, sizeof(Ctrl), g->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->G64, 0, nd, g->stream);
-    if (e == cudaSuccess && g->G32) e = cudaMemsetAsync(g->G32, 0, sizeof(float) * g->N, g->stream);
+    if (e == cudaSuccess && g->own_ctrl) e = cudaMemsetAsync(g->dctrl, 0, sizeof(Ctrl), g->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync((char*)g->G64 - gbytes, 0, 8 * (size_t)g->NA, g->stream);
+    if (e == cudaSuccess && g->G32)
+        e = cudaMemsetAsync((char*)g->G32 - gbytes / 2, 0, 4 * (size_t)g->NA, g->stream);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
-        if (g->y_th[b]) e = cudaMemsetAsync(g->y_th[b], 0, nd, g->stream);
-        if (e == cudaSuccess && g->y_ph[b]) e = cudaMemsetAsync(g->y_ph[b], 0, nd, g->stream);
+        if (g->y_th[b]) e = cudaMemsetAsync((char*)g->y_th[b] - gbytes, 0, 8 * (size_t)g->NA, g->stream);
+        if (e == cudaSuccess && g->y_ph[b]) e = cudaMemsetAsync((char*)g->y_ph[b] - gbytes, 0, 8 * (size_t)g->NA, g->stream);
     }
     if (e != cudaSuccess) {
         destroy_impl(g);
@@ -610,7 +660,7 @@ pf_status pf_create_grid(int n1, int n2, int n3, double h, int model, int reacti
     g->hctrl->theta_thaw = p->theta_thaw;
     g->hctrl->dt_min = p->dt_min;
     g->hctrl->dt_max = p->dt_max;
-    if (push_ctrl(g) != PF_OK || cudaStreamSynchronize(g->stream) != cudaSuccess) {
+    if ((g->own_ctrl && push_ctrl(g) != PF_OK) || cudaStreamSynchronize(g->stream) != cudaSuccess) {
         cudaGetLastError();
         destroy_impl(g);
         return fail(nullptr, PF_E_CUDA, "initialisation failed");
@@ -619,15 +669,22 @@ pf_status pf_create_grid(int n1, int n2, int n3, double h, int model, int reacti
     return PF_OK;
 }
 
+pf_status pf_create_grid(int n1, int n2, int n3, double h, int model, int reaction, int precision,
+                         const pf_params* p, void* stream, pf_grid** out) {
+    return create_impl(n1, n2, n3, h, model, reaction, precision, p, stream, SlabOpts{}, out);
+}
+
 // Derived copies of the glass field: binary32 copy (binary32 form), per-cell coefficients (full model, binary64).
 static pf_status refresh_g32(pf_grid* g) {
+    // over every allocated cell, ghost planes included
+    const long long go = (long long)g->zg_lo * g->n1 * g->n2;
     if (g->statics) {
-        k_full_statics<<<blocks_for(g->N, 256), 256, 0, g->stream>>>(g->G64, g->statics, g->N, g->k64);
+        k_full_statics<<<blocks_for(g->NA, 256), 256, 0, g->stream>>>(g->G64 - go, g->statics - go, g->NA, g->k64);
         count_launch();
         PF_CUDA(g, cudaGetLastError());
     }
     if (!g->G32) return PF_OK;
-    k_to_f32<<<blocks_for(g->N, 256), 256, 0, g->stream>>>(g->G64, g->G32, g->N);
+    k_to_f32<<<blocks_for(g->NA, 256), 256, 0, g->stream>>>(g->G64 - go, g->G32 - go, g->NA);
     count_launch();
     PF_CUDA(g, cudaGetLastError());
     return PF_OK;
@@ -642,7 +699,10 @@ pf_status pf_set_geometry(pf_grid* g, const double* spheres, long long n, double
             if (!std::isfinite(spheres[4 * s + d])) return fail(g, PF_E_INVALID, "non-finite sphere");
         if (!(spheres[4 * s + 3] > 0)) return fail(g, PF_E_INVALID, "sphere radius must be > 0");
     }
-    PF_CUDA(g, cudaMemsetAsync(g->G64, 0, sizeof(double) * g->N, g->stream));
+    // a z-slab computes its ghost planes too (global plane indices: k_off - zg_lo ...)
+    const long long go = (long long)g->zg_lo * g->n1 * g->n2;
+    const int n3a = g->n3 + g->zg_lo + g->zg_hi, kofs = g->k_off - g->zg_lo;
+    PF_CUDA(g, cudaMemsetAsync(g->G64 - go, 0, sizeof(double) * g->NA, g->stream));
     if (n > 0) {
         double* dsp = nullptr;
         PF_CUDA(g, cudaMalloc(&dsp, sizeof(double) * 4 * n));
@@ -651,8 +711,8 @@ pf_status pf_set_geometry(pf_grid* g, const double* spheres, long long n, double
             const long long chunk = 1LL << 30;
             for (long long s0 = 0; s0 < n && e == cudaSuccess; s0 += chunk) {
                 long long cnt = n - s0 < chunk ? n - s0 : chunk;
-                k_glass_spheres<<<(unsigned)cnt, 256, 0, g->stream>>>(dsp + 4 * s0, cnt, g->G64, g->n1, g->n2, g->n3,
-                                                                     g->h, g->p.xi_G);
+                k_glass_spheres<<<(unsigned)cnt, 256, 0, g->stream>>>(dsp + 4 * s0, cnt, g->G64 - go, g->n1, g->n2,
+                                                                     n3a, kofs, g->h, g->p.xi_G);
                 count_launch();
                 e = cudaGetLastError();
             }
@@ -663,7 +723,8 @@ pf_status pf_set_geometry(pf_grid* g, const double* spheres, long long n, double
             return fail(g, PF_E_CUDA, std::string("glass field: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
     if (!std::isnan(x3_cap)) {
-        k_glass_cap<<<blocks_for(g->N, 256), 256, 0, g->stream>>>(g->G64, g->n1, g->n2, g->n3, g->h, g->p.xi_G, x3_cap);
+        k_glass_cap<<<blocks_for(g->NA, 256), 256, 0, g->stream>>>(g->G64 - go, g->n1, g->n2, n3a, kofs, g->h,
+                                                                   g->p.xi_G, x3_cap);
         count_launch();
         PF_CUDA(g, cudaGetLastError());
     }
@@ -706,6 +767,7 @@ pf_status pf_set_state(pf_grid* g, const double* theta, const double* phi, doubl
     c->err_bits = 0;
     c->ice_count = 0;
     c->pore_count = 0;
+    c->rate_bits = 0;
     c->prev_count = -1;
     c->done = 0;
     c->status = 0;
@@ -1383,8 +1445,8 @@ pf_status pf_batch_autotune(pf_batch* b, const char* cache_path) {
     return batch_upload(b);
 }
 
-pf_status pf_batch_run_to(pf_batch* b, const double* t_end, const double* eq_window, double eq_rel_tol, double tol,
-                          long long max_steps, pf_batch_result* res) {
+pf_status pf_batch_run_to(pf_batch* b, const double* t_end, const double* eq_window, double eq_rel_tol,
+                          const double* eq_rate, double tol, long long max_steps, pf_batch_result* res) {
     if (!b) return bfail(nullptr, PF_E_INVALID, "batch is NULL");
     if (!(eq_rel_tol >= 0.0)) return bfail(b, PF_E_INVALID, "eq_rel_tol must be >= 0");
     if (!t_end || !(tol > 0) || max_steps < 1) return bfail(b, PF_E_INVALID, "t_end, tol > 0, max_steps >= 1 required");
@@ -1403,9 +1465,11 @@ pf_status pf_batch_run_to(pf_batch* b, const double* t_end, const double* eq_win
         c->err_bits = 0;
         c->ice_count = 0;
         c->pore_count = 0;
+        c->rate_bits = 0;
         c->prev_count = -1;
         c->eq_window = eq_window ? eq_window[q] : 0.0;
         c->eq_rel_tol = eq_rel_tol;
+        c->eq_rate = eq_rate ? eq_rate[q] : 0.0;
         c->equilibrium = 0;
         c->t_eq = NAN;
         c->done = (c->t < t_end[q]) ? 0 : 1;
@@ -1437,6 +1501,7 @@ pf_status pf_batch_run_to(pf_batch* b, const double* t_end, const double* eq_win
             res[q].stats.last_err = c->last_err;
             res[q].stats.launches = 0;
             res[q].t_eq = c->equilibrium ? c->t_eq : NAN;
+            res[q].rate = c->last_rate;
             res[q].equilibrium = c->equilibrium;
             res[q].status = c->status;
         }
@@ -1445,5 +1510,354 @@ pf_status pf_batch_run_to(pf_batch* b, const double* t_end, const double* eq_win
 }
 
 long long pf_batch_iterations(const pf_batch* b) { return b ? b->iters : -1; }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ z-slab multi-domain mode
+// The paper's parallel layer (Sec. 2.5): the domain is cut along x3 into slabs, each stage's input
+// planes next to a cut are exchanged with the neighbour slab, and the step control uses the error
+// maximum over all slabs.  Here every slab is a grid with ghost planes in one process on one GPU:
+// the exchange is a copy kernel after each stage, the slabs share one control block (so the
+// error maximum and the pore counts accumulate over all slabs and one controller decides).
+
+namespace {
+// Pointers (local plane 0) of one slab's exchanged buffers: [theta, phi][y0, y1, ua, ub].
+struct SlabTab {
+    void* f[2][4];
+    int n3;
+    int pad;
+};
+
+// which: 0 = ua, 1 = ub (stage inputs written by the stage just run), 2 = y[cur ^ 1] (the step's
+// candidate state), 3 = y[cur] (the state).  blockIdx.y = cut * 4 + direction * 2 + field.
+template <typename TF>
+__global__ void k_halo(const SlabTab* __restrict__ tab, long long plane, int which, int fields,
+                       const Ctrl* __restrict__ c) {
+    const int r = blockIdx.y;
+    const int cut = r >> 2, dir = (r >> 1) & 1, f = r & 1;
+    if (!((fields >> f) & 1)) return;
+    const int slot = which < 2 ? 2 + which : (which == 2 ? (c->cur ^ 1) : c->cur);
+    const SlabTab& lo = tab[cut];
+    const SlabTab& hi = tab[cut + 1];
+    const TF* src;
+    TF* dst;
+    if (dir == 0) {  // top plane of the lower slab -> ghost plane below the upper slab
+        src = (const TF*)lo.f[f][slot] + (long long)(lo.n3 - 1) * plane;
+        dst = (TF*)hi.f[f][slot] - plane;
+    } else {         // bottom plane of the upper slab -> ghost plane above the lower slab
+        src = (const TF*)hi.f[f][slot];
+        dst = (TF*)lo.f[f][slot] + (long long)lo.n3 * plane;
+    }
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < plane; q += (long long)gridDim.x * blockDim.x)
+        dst[q] = src[q];
+}
+}  // namespace
+
+struct pf_slabs {
+    int P = 0;
+    int n1 = 0, n2 = 0, n3 = 0;
+    std::vector<int> kb;            // plane boundaries, P + 1 values from 0 to n3
+    std::vector<pf_grid*> s;        // slab 0 owns the shared control block
+    SlabTab* d_tab = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    long long halo_bytes = 0;       // bytes the halo exchanges of the last run moved
+    std::string err;
+};
+
+static pf_status sfail(pf_slabs* S, pf_status st, const std::string& m) {
+    if (S) S->err = m;
+    else t_create_err = m;
+    return st;
+}
+
+#define PF_SCUDA(S, call)                                                                              \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) return sfail((S), PF_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// bytes one exchange moves (every cut, both directions, integrated fields)
+static long long halo_exchange_bytes(const pf_slabs* S, int which) {
+    const pf_grid* g = S->s[0];
+    const int nf = (has_th(g) ? 1 : 0) + (has_ph(g) ? 1 : 0);
+    const size_t esz = which < 2 ? fbytes(g) : sizeof(double);
+    return (long long)(S->P - 1) * 2 * nf * (long long)esz * S->n1 * S->n2;
+}
+
+static cudaError_t halo(pf_slabs* S, int which, cudaStream_t st) {
+    if (S->P < 2) return cudaSuccess;
+    const pf_grid* g = S->s[0];
+    const long long plane = (long long)S->n1 * S->n2;
+    const int fields = (has_th(g) ? 1 : 0) | (has_ph(g) ? 2 : 0);
+    dim3 grid((unsigned)std::min<long long>((plane + 255) / 256, 1024), (unsigned)(4 * (S->P - 1)));
+    if (which >= 2 || !is_f32(g))
+        k_halo<double><<<grid, 256, 0, st>>>(S->d_tab, plane, which, fields, g->dctrl);
+    else
+        k_halo<float><<<grid, 256, 0, st>>>(S->d_tab, plane, which, fields, g->dctrl);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// One Merson attempt over all slabs: each stage on every slab, then the exchange of the planes the
+// next stage reads at the cuts; the controller once (shared control block).
+static cudaError_t slabs_enqueue_attempt(pf_slabs* S, cudaStream_t st) {
+    for (int stage = 1; stage <= 5; ++stage) {
+        for (pf_grid* g : S->s) {
+            cudaError_t e = launch_stage(g, stage, st);
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = halo(S, stage == 5 ? 2 : (stage % 2 == 1 ? 0 : 1), st);
+        if (e != cudaSuccess) return e;
+    }
+    k_controller<<<1, 32, 0, st>>>(S->s[0]->dctrl);
+    count_launch();
+    return cudaGetLastError();
+}
+
+static long long slabs_attempt_launches(const pf_slabs* S) { return 5LL * (S->P + (S->P > 1 ? 1 : 0)) + 1; }
+
+static void slabs_free_graph(pf_slabs* S) {
+    if (S->graph) cudaGraphExecDestroy(S->graph);
+    S->graph = nullptr;
+    S->graph_steps = 0;
+}
+
+static pf_status slabs_build_graph(pf_slabs* S, int steps) {
+    slabs_free_graph(S);
+    pf_grid* g0 = S->s[0];
+    cudaGraph_t graph = nullptr;
+    PF_SCUDA(S, cudaStreamBeginCapture(g0->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < steps && e == cudaSuccess; ++q) e = slabs_enqueue_attempt(S, g0->cap_stream);
+    cudaError_t e2 = cudaStreamEndCapture(g0->cap_stream, &graph);
+    // launches made during capture are only recorded, not executed
+    pfgb::g_launches.fetch_sub((long long)steps * slabs_attempt_launches(S), std::memory_order_relaxed);
+    for (pf_grid* g : S->s) g->launches -= (long long)steps * 5;
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return sfail(S, PF_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaError_t e3 = cudaGraphInstantiate(&S->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e3 != cudaSuccess) {
+        S->graph = nullptr;
+        return sfail(S, PF_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e3));
+    }
+    S->graph_steps = steps;
+    return PF_OK;
+}
+
+static void slabs_destroy_impl(pf_slabs* S) {
+    slabs_free_graph(S);
+    // slabs other than 0 borrow slab 0's control block: destroy them first
+    for (int q = (int)S->s.size() - 1; q >= 0; --q)
+        if (S->s[q]) destroy_impl(S->s[q]);
+    if (S->d_tab) cudaFree(S->d_tab);
+    delete S;
+}
+
+extern "C" {
+
+const char* pf_slabs_last_error(const pf_slabs* S) { return S ? S->err.c_str() : t_create_err.c_str(); }
+
+pf_status pf_slabs_create(int n1, int n2, int n3, double h, int model, int reaction, int precision,
+                          const pf_params* p, int nslabs, const int* planes, void* stream, pf_slabs** out) {
+    if (!out) return sfail(nullptr, PF_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (nslabs < 1 || nslabs > 1024 || n3 < nslabs) return sfail(nullptr, PF_E_INVALID, "need 1 <= nslabs <= n3");
+    std::vector<int> kb(nslabs + 1);
+    for (int q = 0; q <= nslabs; ++q) kb[q] = planes ? planes[q] : (int)((long long)n3 * q / nslabs);
+    if (kb[0] != 0 || kb[nslabs] != n3) return sfail(nullptr, PF_E_INVALID, "planes must run from 0 to n3");
+    for (int q = 0; q < nslabs; ++q)
+        if (kb[q + 1] <= kb[q]) return sfail(nullptr, PF_E_INVALID, "every slab needs at least one plane");
+    pf_slabs* S = new pf_slabs();
+    S->P = nslabs;
+    S->n1 = n1; S->n2 = n2; S->n3 = n3;
+    S->kb = kb;
+    S->s.assign(nslabs, nullptr);
+    for (int q = 0; q < nslabs; ++q) {
+        SlabOpts so;
+        so.zg_lo = q > 0 ? 1 : 0;
+        so.zg_hi = q < nslabs - 1 ? 1 : 0;
+        so.k_off = kb[q];
+        so.ctrl_owner = q > 0 ? S->s[0] : nullptr;
+        pf_status st = create_impl(n1, n2, kb[q + 1] - kb[q], h, model, reaction, precision, p, stream, so, &S->s[q]);
+        if (st != PF_OK) {
+            const std::string m = t_create_err;
+            slabs_destroy_impl(S);
+            return sfail(nullptr, st, "slab " + std::to_string(q) + ": " + m);
+        }
+    }
+    std::vector<SlabTab> tab(nslabs);
+    for (int q = 0; q < nslabs; ++q) {
+        pf_grid* g = S->s[q];
+        SlabTab& t = tab[q];
+        t.f[0][0] = g->y_th[0]; t.f[0][1] = g->y_th[1]; t.f[0][2] = g->ua_th; t.f[0][3] = g->ub_th;
+        t.f[1][0] = g->y_ph[0]; t.f[1][1] = g->y_ph[1]; t.f[1][2] = g->ua_ph; t.f[1][3] = g->ub_ph;
+        t.n3 = g->n3;
+        t.pad = 0;
+    }
+    if (cudaMalloc(&S->d_tab, sizeof(SlabTab) * nslabs) != cudaSuccess ||
+        cudaMemcpy(S->d_tab, tab.data(), sizeof(SlabTab) * nslabs, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        slabs_destroy_impl(S);
+        return sfail(nullptr, PF_E_OOM, "slab table allocation failed");
+    }
+    *out = S;
+    return PF_OK;
+}
+
+pf_status pf_slabs_destroy(pf_slabs* S) {
+    if (!S) return PF_OK;
+    cudaStreamSynchronize(S->s[0]->stream);
+    slabs_destroy_impl(S);
+    return PF_OK;
+}
+
+pf_grid* pf_slabs_grid(pf_slabs* S, int q) {
+    if (!S || q < 0 || q >= S->P) return nullptr;
+    return S->s[q];
+}
+
+pf_status pf_slabs_set_geometry(pf_slabs* S, const double* spheres, long long n, double x3_cap) {
+    if (!S) return sfail(nullptr, PF_E_INVALID, "slabs is NULL");
+    for (pf_grid* g : S->s) {
+        pf_status st = pf_set_geometry(g, spheres, n, x3_cap);
+        if (st != PF_OK) return sfail(S, st, g->err);
+    }
+    return PF_OK;
+}
+
+pf_status pf_slabs_set_tiles(pf_slabs* S, int by, int zc) {
+    if (!S) return sfail(nullptr, PF_E_INVALID, "slabs is NULL");
+    for (pf_grid* g : S->s) {
+        pf_status st = set_tiles_impl(g, by, zc);
+        if (st != PF_OK) return sfail(S, st, g->err);
+    }
+    slabs_free_graph(S);
+    return PF_OK;
+}
+
+pf_status pf_slabs_set_state(pf_slabs* S, const double* theta, const double* phi, double t, double dt) {
+    if (!S) return sfail(nullptr, PF_E_INVALID, "slabs is NULL");
+    pf_grid* g0 = S->s[0];
+    if (has_th(g0) && !theta) return sfail(S, PF_E_INVALID, "theta is NULL");
+    if (has_ph(g0) && !phi) return sfail(S, PF_E_INVALID, "phi is NULL");
+    const long long plane = (long long)S->n1 * S->n2;
+    for (int q = S->P - 1; q >= 0; --q) {  // slab 0 last: its pf_set_state resets the shared control block
+        pf_grid* g = S->s[q];
+        const long long off = (long long)S->kb[q] * plane;
+        if (q == 0) {
+            pf_status st = pf_set_state(g, theta ? theta + off : nullptr, phi ? phi + off : nullptr, t, dt);
+            if (st != PF_OK) return sfail(S, st, g->err);
+        } else {
+            if (has_th(g)) PF_SCUDA(S, cudaMemcpyAsync(g->y_th[0], theta + off, sizeof(double) * g->N, cudaMemcpyHostToDevice, g->stream));
+            if (has_ph(g)) PF_SCUDA(S, cudaMemcpyAsync(g->y_ph[0], phi + off, sizeof(double) * g->N, cudaMemcpyHostToDevice, g->stream));
+        }
+    }
+    PF_SCUDA(S, halo(S, 3, g0->stream));
+    PF_SCUDA(S, cudaStreamSynchronize(g0->stream));
+    return PF_OK;
+}
+
+pf_status pf_slabs_get_state(pf_slabs* S, double* theta, double* phi, double* t, double* dt) {
+    if (!S) return sfail(nullptr, PF_E_INVALID, "slabs is NULL");
+    pf_grid* g0 = S->s[0];
+    pf_status st = sync_ctrl_to_host(g0);
+    if (st != PF_OK) return sfail(S, st, g0->err);
+    const int cur = g0->hctrl->cur;
+    const long long plane = (long long)S->n1 * S->n2;
+    for (int q = 0; q < S->P; ++q) {
+        pf_grid* g = S->s[q];
+        const long long off = (long long)S->kb[q] * plane;
+        if (theta && has_th(g))
+            PF_SCUDA(S, cudaMemcpyAsync(theta + off, g->y_th[cur], sizeof(double) * g->N, cudaMemcpyDeviceToHost, g->stream));
+        if (phi && has_ph(g))
+            PF_SCUDA(S, cudaMemcpyAsync(phi + off, g->y_ph[cur], sizeof(double) * g->N, cudaMemcpyDeviceToHost, g->stream));
+    }
+    PF_SCUDA(S, cudaStreamSynchronize(g0->stream));
+    if (theta && !has_th(g0)) for (long long q = 0; q < (long long)S->n3 * plane; ++q) theta[q] = g0->p.theta_micro;
+    if (t) *t = g0->hctrl->t;
+    if (dt) *dt = g0->hctrl->dt;
+    return PF_OK;
+}
+
+pf_status pf_slabs_run_to(pf_slabs* S, double t_end, double tol, long long max_steps, pf_run_stats* stats) {
+    if (!S) return sfail(nullptr, PF_E_INVALID, "slabs is NULL");
+    if (!(tol > 0) || std::isnan(t_end)) return sfail(S, PF_E_INVALID, "tol must be > 0 and t_end a number");
+    pf_grid* g0 = S->s[0];
+    pf_status st = sync_ctrl_to_host(g0);
+    if (st != PF_OK) return sfail(S, st, g0->err);
+    Ctrl* c = g0->hctrl;
+    c->t_end = t_end;
+    c->tol = tol;
+    c->fixed = 0;
+    c->eq_window = 0.0;
+    c->equilibrium = 0;
+    c->single = 0;
+    c->max_attempts = max_steps;
+    c->n_acc = c->n_rej = 0;
+    c->status = 0;
+    c->err_bits = 0;
+    S->halo_bytes = 0;
+    if (!(c->t < t_end) || max_steps <= 0) {
+        if (stats) *stats = {0, 0, c->t, c->dt, c->last_err, 0};
+        return PF_OK;
+    }
+    c->done = 0;
+    first_step(c);
+    const int steps_per_graph = max_steps >= 16 ? 16 : (max_steps >= 4 ? 4 : 1);
+    if (!S->graph || S->graph_steps != steps_per_graph) {
+        st = slabs_build_graph(S, steps_per_graph);
+        if (st != PF_OK) return st;
+    }
+    st = push_ctrl(g0);
+    if (st != PF_OK) return sfail(S, st, g0->err);
+    long long launched = 0, replays = 0;
+    for (;;) {
+        PF_SCUDA(S, cudaGraphLaunch(S->graph, g0->stream));
+        launched += steps_per_graph * slabs_attempt_launches(S);
+        ++replays;
+        st = sync_ctrl_to_host(g0);
+        if (st != PF_OK) return sfail(S, st, g0->err);
+        if (c->done) break;
+    }
+    count_launch(launched);
+    // every replayed attempt exchanges the five stages' planes (attempts after the run ended copy
+    // unchanged planes)
+    long long per_attempt = 0;
+    for (int w : {0, 1, 0, 1, 2}) per_attempt += halo_exchange_bytes(S, w);
+    S->halo_bytes = replays * steps_per_graph * per_attempt;
+    if (stats) {
+        stats->n_accepted = c->n_acc;
+        stats->n_rejected = c->n_rej;
+        stats->t = c->t;
+        stats->dt = c->dt;
+        stats->last_err = c->last_err;
+        stats->launches = launched;
+    }
+    if (c->status == PF_E_DT_UNDERFLOW) return sfail(S, PF_E_DT_UNDERFLOW, "step size fell below dt_min");
+    if (c->status == PF_E_NONFINITE) return sfail(S, PF_E_NONFINITE, "non-finite error estimate");
+    return PF_OK;
+}
+
+pf_status pf_slabs_unfrozen_fraction(pf_slabs* S, double* uwc, long long* n_ice, long long* n_water) {
+    if (!S) return sfail(nullptr, PF_E_INVALID, "slabs is NULL");
+    long long ni = 0, nw = 0;
+    for (pf_grid* g : S->s) {
+        long long a = 0, b = 0;
+        pf_status st = pf_unfrozen_fraction(g, nullptr, nullptr, &a, &b, nullptr);
+        if (st != PF_OK) return sfail(S, st, g->err);
+        ni += a;
+        nw += b;
+    }
+    if (n_ice) *n_ice = ni;
+    if (n_water) *n_water = nw;
+    if (uwc) *uwc = nw ? 1.0 - (double)ni / (double)nw : NAN;
+    return PF_OK;
+}
+
+long long pf_slabs_halo_bytes(const pf_slabs* S) { return S ? S->halo_bytes : -1; }
 
 }  // extern "C"

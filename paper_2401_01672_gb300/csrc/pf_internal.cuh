@@ -12,6 +12,9 @@ enum { R_SIGMA = 0, R_GRADP = 1 };
 // each thread marches along z over a chunk of ZC planes.
 constexpr int TX = 32;
 
+// per-cell coefficient arrays of the binary64 full model (see StageArgs::statics)
+constexpr int NSTATIC = 10;
+
 // Model constants in the form the stage kernels use them, filled on the host
 // (binary64 arithmetic) for each field type, so kernels convert nothing.
 //   lambda = lamL + G dLG + (1 - G) phi dLI, scaled by 1/(2 h^2)  (eq. material-properties-blending-formula)
@@ -39,6 +42,8 @@ struct Coefs {
     int n1, n2, n3;
     int dirichlet;      // PF_FACE_* bits
     int harmonic;       // face conductivity: harmonic mean
+    int zlo, zhi;       // planes the z neighbours are clamped to: 0 and n3 - 1 (mirror ghosts at both ends);
+                        // -1 / n3 where a z-slab has a ghost plane filled by its neighbour
     int pad0;
     double theta_freeze, theta_thaw, t_freeze;
 };
@@ -65,6 +70,9 @@ struct Ctrl {
     unsigned long long err_bits;  // max of the error estimate over cells (bit pattern of a double >= 0)
     unsigned long long ice_count; // stage 1: #{phi > 1/2 and G < 1/(2 zeta)} of the current state (pore bulk)
     unsigned long long pore_count; // stage 1: #{G < 1/(2 zeta)} (pore-bulk cells)
+    unsigned long long rate_bits;  // stage 1: max |dphi/dt| over the pore-bulk cells (bit pattern of a double)
+    double eq_rate;               // equilibrium also needs that maximum <= eq_rate (0 = no residual test)
+    double last_rate;             // the maximum of the last attempt
     long long prev_count;         // ice count when it last changed by more than the tolerance (-1: none yet)
     double eq_rel_tol;            // tolerated change of the ice count, relative to the pore-bulk cells
     double last_change_t;         // time of that change
@@ -124,9 +132,10 @@ struct StageArgs {
     T* k3_th; T* k3_ph;
     T* k4_th; T* k4_ph;
     const T* G;              // glass field
-    // full model, binary64: per-cell coefficients precomputed from G (SoA, 8 arrays of n cells):
+    // full model, binary64: per-cell coefficients precomputed from G (SoA, NSTATIC arrays of n cells):
     // [0] A_lam [1] B_lam (lambda' = A + B phi)  [2] W = 2 I_W/(alpha xi^2) before the max
     // [3..5] C0, C1, C2 (rho c = C0 + phi (C1 + phi C2))  [6..7] D0, D1 (rho L = D0 + D1 phi)
+    // [8..9] 1/(rho c) at phi = 0 and at phi = 1
     const double* statics;
     long long ncell;
     // plain right-hand side (stage 0)

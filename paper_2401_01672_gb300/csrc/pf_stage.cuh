@@ -20,7 +20,8 @@
 // (binary32 stages 2-4: one plane ahead), so memory latency overlaps computation.
 // Cells outside the grid are replaced by the nearest boundary cell (mirror ghost),
 // which makes the interior formula give zero flux on every face; Dirichlet faces
-// add their half-cell flux separately.
+// add their half-cell flux separately.  A z-slab of a multi-domain run instead reads
+// the ghost plane its neighbour slab fills (Coefs::zlo, zhi).
 //
 // Binary64 operation count: the binary64 pipe of sm_103a issues two FMAs per clock
 // per SM, a sixtieth of the binary32 rate, so the binary64 kernels keep every
@@ -148,6 +149,27 @@ __device__ __forceinline__ T water_ind(T G, T zeta) {
     return positive(v) ? v : T(0);
 }
 
+// phi of a cell and of its six neighbours all exactly +0 or all exactly 1 (IEEE bit patterns, integer
+// instructions only).  There the Laplacian is 0 and the reaction term 2 phi (1 - phi)(...) is 0, so
+// dphi/dt = 0 exactly (eq. Allen-Cahn-equation): the bulk of the water and of the ice.
+__device__ __forceinline__ bool uniform_01(double c, double a0, double a1, double a2, double a3, double a4,
+                                           double a5) {
+    const long long cb = __double_as_longlong(c);
+    bool r = (cb == 0LL) | (cb == 0x3FF0000000000000LL);
+    r &= (__double_as_longlong(a0) == cb) & (__double_as_longlong(a1) == cb) & (__double_as_longlong(a2) == cb);
+    r &= (__double_as_longlong(a3) == cb) & (__double_as_longlong(a4) == cb) & (__double_as_longlong(a5) == cb);
+    return r;
+}
+__device__ __forceinline__ bool uniform_01(float c, float a0, float a1, float a2, float a3, float a4, float a5) {
+    const int cb = __float_as_int(c);
+    bool r = (cb == 0) | (cb == 0x3F800000);
+    r &= (__float_as_int(a0) == cb) & (__float_as_int(a1) == cb) & (__float_as_int(a2) == cb);
+    r &= (__float_as_int(a3) == cb) & (__float_as_int(a4) == cb) & (__float_as_int(a5) == cb);
+    return r;
+}
+__device__ __forceinline__ bool is_one(double v) { return __double_as_longlong(v) == 0x3FF0000000000000LL; }
+__device__ __forceinline__ bool is_one(float v) { return __float_as_int(v) == 0x3F800000; }
+
 template <typename T>
 __device__ __forceinline__ unsigned long long abs_bits(T v) {
     if constexpr (std::is_same<T, double>::value) {
@@ -247,7 +269,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
     // (theta and phi stay in the input type until `cvt`, so that a conversion does not wait for its
     // load where the load is issued)
     auto fetch = [&](int kk, long long off, TIN& th, TIN& ph, T& G, T& B) {
-        const long long id = (long long)min(max(kk, 0), n3 - 1) * plane + off;
+        const long long id = (long long)min(max(kk, a.cf.zlo), a.cf.zhi) * plane + off;
         if constexpr (STATIC) {
             G = T(St[id]);
             B = T(St[NC + id]);
@@ -347,6 +369,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
 
     unsigned long long ebits = 0ULL;  // max |E| as a bit pattern (NaN/Inf sort above every finite value)
     unsigned int icount = 0, pcount = 0;  // stage 1: pore-bulk ice cells and pore-bulk cells of this thread
+    unsigned long long rbits = 0ULL;      // stage 1: max |dphi/dt| over this thread's pore-bulk cells
     int b = 0;
 
 #pragma unroll 3
@@ -358,11 +381,21 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
         if (hal) fetch(k + 2, hoff, qth, qph, qG, qB);
 
         const long long id = (long long)k * plane + (long long)j * n1 + i;
+        // phase field of the lateral neighbours (Laplacian, gradient) and the bulk test
+        // (binary64 only: its integer test is free next to the binary64 arithmetic it can save, while
+        // the binary32 kernels are bound by memory and instruction issue, where the test costs more)
+        T p_xm = T(0), p_xp = T(0), p_ym = T(0), p_yp = T(0);
+        bool bulk = false;
+        if constexpr (!TEMP && !F32) {
+            p_xm = s_ph[b][ty + 1][tx]; p_xp = s_ph[b][ty + 1][tx + 2];
+            p_ym = s_ph[b][ty][tx + 1]; p_yp = s_ph[b][ty + 2][tx + 1];
+            bulk = uniform_01(phc, p_xm, p_xp, p_ym, p_yp, phm, php);
+        }
         // 2. stage-combination operands of this cell
         T y_t = T(0), y_p = T(0), k1t = T(0), k1p = T(0), k3t = T(0), k3p = T(0), k4t = T(0), k4p = T(0);
         double y_t64 = 0.0, y_p64 = 0.0;
         T ua_t = T(0), ua_p = T(0);
-        T sW = T(0), sC0 = T(0), sC1 = T(0), sC2 = T(0), sD0 = T(0), sD1 = T(0);
+        T sW = T(0), sC0 = T(0), sC1 = T(0), sC2 = T(0), sD0 = T(0), sD1 = T(0), sIR = T(0);
         if constexpr (PF) {
             // take the operands loaded during the previous plane, then load those of plane k+1
             k1t = n_k1t; k1p = n_k1p; k3t = n_k3t; k3p = n_k3p; ua_t = n_uat; ua_p = n_uap;
@@ -401,9 +434,14 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
                 if constexpr (HAS_PH) ua_p = a.ua_ph[id];
             }
             if constexpr (STATIC) {
-                sW = St[2 * NC + id];
-                sC0 = St[3 * NC + id]; sC1 = St[4 * NC + id]; sC2 = St[5 * NC + id];
-                sD0 = St[6 * NC + id]; sD1 = St[7 * NC + id];
+                // a bulk cell needs only 1/(rho c) at its phi; stage 1 also counts the pore cells (W)
+                if (STAGE == 1 || !bulk) sW = St[2 * NC + id];
+                if (bulk) {
+                    sIR = St[(is_one(phc) ? 9 : 8) * NC + id];
+                } else {
+                    sC0 = St[3 * NC + id]; sC1 = St[4 * NC + id]; sC2 = St[5 * NC + id];
+                    sD0 = St[6 * NC + id]; sD1 = St[7 * NC + id];
+                }
             }
         }
 
@@ -443,12 +481,16 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
             // ---- Allen-Cahn rate (eq. Allen-Cahn-equation): dphi = W (klap lap + f/2), W = 2 I_W/(alpha xi^2)
             T dph = T(0);
             if constexpr (!TEMP) {
-                T W;
-                if constexpr (STATIC) W = sW;
-                else W = FMA(K.wb, Gc, K.wa);
+                T W = T(0);
+                if (!bulk) {  // bulk cells: dphi = 0 without arithmetic
+                    if constexpr (STATIC) W = sW;
+                    else W = FMA(K.wb, Gc, K.wa);
+                }
                 if (positive(W)) {
-                    const T p_xm = s_ph[b][ty + 1][tx], p_xp = s_ph[b][ty + 1][tx + 2];
-                    const T p_ym = s_ph[b][ty][tx + 1], p_yp = s_ph[b][ty + 2][tx + 1];
+                    if constexpr (F32) {
+                        p_xm = s_ph[b][ty + 1][tx]; p_xp = s_ph[b][ty + 1][tx + 2];
+                        p_ym = s_ph[b][ty][tx + 1]; p_yp = s_ph[b][ty + 2][tx + 1];
+                    }
                     const T lsum = ((p_xm + p_xp) + (p_ym + p_yp)) + (phm + php);
                     const T lap = FMA(T(-6), phc, lsum);
                     const T om = T(1) - phc;
@@ -472,8 +514,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
             // ---- latent-heat coupling
             T dth = T(0);
             if constexpr (STATIC) {
-                const T rhoc = FMA(phc, FMA(phc, sC2, sC1), sC0);
-                dth = FMA(FMA(phc, sD1, sD0), dph, div) * recip_pos(rhoc);
+                if (bulk) {
+                    dth = div * sIR;  // dphi = 0
+                } else {
+                    const T rhoc = FMA(phc, FMA(phc, sC2, sC1), sC0);
+                    dth = FMA(FMA(phc, sD1, sD0), dph, div) * recip_pos(rhoc);
+                }
             } else if constexpr (MODEL == M_FULL) {
                 const T rho = blend3(Gc, phc, K.rhoL, K.dRG, K.dRI);
                 const T cp = blend3(Gc, phc, K.capL, K.dCG, K.dCI);
@@ -502,6 +548,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
                     if (in_pore) {
                         ++pcount;
                         if (!le_nonneg(phc, T(0.5))) ++icount;
+                        const unsigned long long rb = abs_bits(dph);
+                        rbits = rb > rbits ? rb : rbits;
                     }
                 }
             } else if constexpr (STAGE == 2) {
@@ -597,23 +645,36 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
         }
     }
     if constexpr (STAGE == 1 && HAS_PH) {
-        // block sums of the two counts -> one atomicAdd each
+        // block sums of the two counts -> one atomicAdd each; block max of |dphi/dt| -> one atomicMax
         unsigned int ci = icount, cp = pcount;
+        unsigned long long r = rbits;
+        if constexpr (F32) {
+            const unsigned fb = (unsigned)r;
+            r = (fb >= 0x7F800000u) ? 0x7FF0000000000000ULL
+                                    : (unsigned long long)__double_as_longlong((double)__uint_as_float(fb));
+        }
         for (int o = 16; o > 0; o >>= 1) {
             ci += __shfl_xor_sync(0xffffffffu, ci, o);
             cp += __shfl_xor_sync(0xffffffffu, cp, o);
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, r, o);
+            r = v > r ? v : r;
         }
         __shared__ unsigned int s_cnt[2][BY];
-        if (tx == 0) { s_cnt[0][ty] = ci; s_cnt[1][ty] = cp; }
+        __shared__ unsigned long long s_rate[BY];
+        if (tx == 0) { s_cnt[0][ty] = ci; s_cnt[1][ty] = cp; s_rate[ty] = r; }
         __syncthreads();
         if (ty == 0) {
             unsigned int v = tx < BY ? s_cnt[0][tx] : 0u, w = tx < BY ? s_cnt[1][tx] : 0u;
+            unsigned long long m = tx < BY ? s_rate[tx] : 0ULL;
             for (int o = 16; o > 0; o >>= 1) {
                 v += __shfl_xor_sync(0xffffffffu, v, o);
                 w += __shfl_xor_sync(0xffffffffu, w, o);
+                const unsigned long long x = __shfl_xor_sync(0xffffffffu, m, o);
+                m = x > m ? x : m;
             }
             if (tx == 0 && v > 0u) atomicAdd(&ctrl->ice_count, (unsigned long long)v);
             if (tx == 0 && w > 0u) atomicAdd(&ctrl->pore_count, (unsigned long long)w);
+            if (tx == 0 && m > 0ULL) atomicMax(&ctrl->rate_bits, m);
         }
     }
     __syncthreads();  // the block may start another tile: shared memory is reused
@@ -626,12 +687,20 @@ stage_kernel(const StageArgs<T> a) {
     stage_tile<MODEL, RX, T, TIN, STAGE, BY>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
+// Binary64 form: at most 128 registers per thread, so that 16 warps of every block shape stay resident
+// on an SM (measured faster than one 8-warp block at 136 registers).  The binary32 kernels keep the
+// compiler's own register choice (an explicit bound, even of one block, made it take more registers).
+template <int MODEL, int RX, typename T, typename TIN, int STAGE, int BY>
+__global__ void __launch_bounds__(TX * BY, 16 / BY)
+stage_kernel_r128(const StageArgs<T> a) {
+    stage_tile<MODEL, RX, T, TIN, STAGE, BY>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // Batched persistent form: a fixed grid of blocks walks, in order, the tiles of the instances
 // listed in the plan (instances that are finished are not listed).
 template <int MODEL, int RX, typename T, typename TIN, int STAGE, int BY>
-__global__ void __launch_bounds__(TX * BY)
-batch_stage_kernel(const StageArgs<T>* __restrict__ args, const BatchPlan* __restrict__ plan,
-                   const int4* __restrict__ tilegrid) {
+__device__ __forceinline__ void batch_tiles(const StageArgs<T>* __restrict__ args, const BatchPlan* __restrict__ plan,
+                                            const int4* __restrict__ tilegrid) {
     const int nt = plan->ntiles;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         int s = 0;
@@ -642,6 +711,118 @@ batch_stage_kernel(const StageArgs<T>* __restrict__ args, const BatchPlan* __res
         stage_tile<MODEL, RX, T, TIN, STAGE, BY>(args[inst], local % tg.x, (local / tg.x) % tg.y,
                                                   local / (tg.x * tg.y));
     }
+}
+
+template <int MODEL, int RX, typename T, typename TIN, int STAGE, int BY>
+__global__ void __launch_bounds__(TX * BY)
+batch_stage_kernel(const StageArgs<T>* __restrict__ args, const BatchPlan* __restrict__ plan,
+                   const int4* __restrict__ tilegrid) {
+    batch_tiles<MODEL, RX, T, TIN, STAGE, BY>(args, plan, tilegrid);
+}
+
+template <int MODEL, int RX, typename T, typename TIN, int STAGE, int BY>
+__global__ void __launch_bounds__(TX * BY, 16 / BY)
+batch_stage_kernel_r128(const StageArgs<T>* __restrict__ args, const BatchPlan* __restrict__ plan,
+                        const int4* __restrict__ tilegrid) {
+    batch_tiles<MODEL, RX, T, TIN, STAGE, BY>(args, plan, tilegrid);
+}
+
+// ---------------------------------------------------------------- launchers (one per field type)
+template <typename T, int MODEL, int RX, int STAGE, int BY>
+void launch_one(const StageArgs<T>& a, dim3 grid, cudaStream_t s) {
+    using TIN = typename std::conditional<STAGE == 1, double, T>::type;
+    if constexpr (std::is_same<T, double>::value)
+        stage_kernel_r128<MODEL, RX, T, TIN, STAGE, BY><<<grid, dim3(TX, BY), 0, s>>>(a);
+    else
+        stage_kernel<MODEL, RX, T, TIN, STAGE, BY><<<grid, dim3(TX, BY), 0, s>>>(a);
+}
+
+template <typename T, int MODEL, int RX, int BY>
+cudaError_t launch_by(int stage, const StageArgs<T>& a, cudaStream_t s) {
+    const int n1 = a.cf.n1, n2 = a.cf.n2, n3 = a.cf.n3;
+    dim3 grid((n1 + TX - 1) / TX, (n2 + BY - 1) / BY, (n3 + a.zc - 1) / a.zc);
+    switch (stage) {
+        case 0: launch_one<T, MODEL, RX, 0, BY>(a, grid, s); break;
+        case 1: launch_one<T, MODEL, RX, 1, BY>(a, grid, s); break;
+        case 2: launch_one<T, MODEL, RX, 2, BY>(a, grid, s); break;
+        case 3: launch_one<T, MODEL, RX, 3, BY>(a, grid, s); break;
+        case 4: launch_one<T, MODEL, RX, 4, BY>(a, grid, s); break;
+        case 5: launch_one<T, MODEL, RX, 5, BY>(a, grid, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T, int MODEL, int RX, int STAGE, int BY>
+void batch_one(const StageArgs<T>* args, const BatchPlan* plan, const int4* tg, int blocks, cudaStream_t s) {
+    using TIN = typename std::conditional<STAGE == 1, double, T>::type;
+    if constexpr (std::is_same<T, double>::value)
+        batch_stage_kernel_r128<MODEL, RX, T, TIN, STAGE, BY><<<blocks, dim3(TX, BY), 0, s>>>(args, plan, tg);
+    else
+        batch_stage_kernel<MODEL, RX, T, TIN, STAGE, BY><<<blocks, dim3(TX, BY), 0, s>>>(args, plan, tg);
+}
+
+template <typename T, int MODEL, int RX, int BY>
+cudaError_t batch_by(int stage, const StageArgs<T>* args, const BatchPlan* plan, const int4* tg, int blocks,
+                     cudaStream_t s) {
+    switch (stage) {
+        case 1: batch_one<T, MODEL, RX, 1, BY>(args, plan, tg, blocks, s); break;
+        case 2: batch_one<T, MODEL, RX, 2, BY>(args, plan, tg, blocks, s); break;
+        case 3: batch_one<T, MODEL, RX, 3, BY>(args, plan, tg, blocks, s); break;
+        case 4: batch_one<T, MODEL, RX, 4, BY>(args, plan, tg, blocks, s); break;
+        case 5: batch_one<T, MODEL, RX, 5, BY>(args, plan, tg, blocks, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+// model, reaction term and block height chosen at run time
+template <typename T>
+cudaError_t launch_stage_t(int model, int rx, int stage, const StageArgs<T>& a, int by, cudaStream_t s) {
+    if (a.zc <= 0) return cudaErrorInvalidValue;
+    auto m = [&](auto M, auto R) -> cudaError_t {
+        constexpr int MO = decltype(M)::value, RO = decltype(R)::value;
+        switch (by) {
+            case 4: return launch_by<T, MO, RO, 4>(stage, a, s);
+            case 8: return launch_by<T, MO, RO, 8>(stage, a, s);
+            case 16: return launch_by<T, MO, RO, 16>(stage, a, s);
+            default: return cudaErrorInvalidValue;
+        }
+    };
+    using F = std::integral_constant<int, M_FULL>;
+    using Tm = std::integral_constant<int, M_TEMP>;
+    using Mi = std::integral_constant<int, M_MICRO>;
+    using Sg = std::integral_constant<int, R_SIGMA>;
+    using Gp = std::integral_constant<int, R_GRADP>;
+    if (model == M_FULL) return rx == R_GRADP ? m(F{}, Gp{}) : m(F{}, Sg{});
+    if (model == M_TEMP) return m(Tm{}, Sg{});
+    if (model == M_MICRO) return rx == R_GRADP ? m(Mi{}, Gp{}) : m(Mi{}, Sg{});
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_batch_stage_t(int model, int rx, int stage, const StageArgs<T>* args, const BatchPlan* plan,
+                                 const int4* tg, int by, int blocks, cudaStream_t s) {
+    auto m = [&](auto M, auto R) -> cudaError_t {
+        constexpr int MO = decltype(M)::value, RO = decltype(R)::value;
+        switch (by) {
+            case 4: return batch_by<T, MO, RO, 4>(stage, args, plan, tg, blocks, s);
+            case 8: return batch_by<T, MO, RO, 8>(stage, args, plan, tg, blocks, s);
+            case 16: return batch_by<T, MO, RO, 16>(stage, args, plan, tg, blocks, s);
+            default: return cudaErrorInvalidValue;
+        }
+    };
+    using F = std::integral_constant<int, M_FULL>;
+    using Tm = std::integral_constant<int, M_TEMP>;
+    using Mi = std::integral_constant<int, M_MICRO>;
+    using Sg = std::integral_constant<int, R_SIGMA>;
+    using Gp = std::integral_constant<int, R_GRADP>;
+    if (model == M_FULL) return rx == R_GRADP ? m(F{}, Gp{}) : m(F{}, Sg{});
+    if (model == M_TEMP) return m(Tm{}, Sg{});
+    if (model == M_MICRO) return rx == R_GRADP ? m(Mi{}, Gp{}) : m(Mi{}, Sg{});
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace pfgb

@@ -3,7 +3,9 @@ phase field from the glass field, the supercooling and the surface-tension scale
 
 Every forward, backward and optimiser operation runs in the library's CUDA kernels (include/pfnn.h):
 BF16 tensor-core 3x3x3 convolutions with FP32 accumulation, pooling/upsampling, the sigmoid head
-with binary cross-entropy, Adam on FP32 master weights.  torch only allocates the device buffers.
+with binary cross-entropy, Adam on FP32 master weights.  The network itself (its layer sequence,
+parameters and buffers) is the library's pfnn_net; this module marshals arguments (torch allocates
+the caller's input and output tensors).
 
 Architecture (4 levels, channels 16/32/64/128, two 3x3x3 convolutions + ReLU per level, 2x2x2
 average-pool down, x2 nearest up + 3x3x3 convolution, skip concatenation, 1x1x1 sigmoid head):
@@ -22,31 +24,6 @@ import numpy as np
 
 from . import pf as _pf
 
-# (name, input buffer, input channel offset, cin, output buffer, output offset, cout, level)
-LAYERS = [
-    ("e1a", "in0", 0, 16, "e1a", 0, 16, 0),
-    ("e1b", "e1a", 0, 16, "cat1", 0, 16, 0),
-    ("e2a", "p1", 0, 16, "e2a", 0, 32, 1),
-    ("e2b", "e2a", 0, 32, "cat2", 0, 32, 1),
-    ("e3a", "p2", 0, 32, "e3a", 0, 64, 2),
-    ("e3b", "e3a", 0, 64, "cat3", 0, 64, 2),
-    ("e4a", "p3", 0, 64, "e4a", 0, 128, 3),
-    ("e4b", "e4a", 0, 128, "e4b", 0, 128, 3),
-    ("u3", "up3", 0, 128, "cat3", 64, 64, 2),
-    ("d3a", "cat3", 0, 128, "d3a", 0, 64, 2),
-    ("d3b", "d3a", 0, 64, "d3b", 0, 64, 2),
-    ("u2", "up2", 0, 64, "cat2", 32, 32, 1),
-    ("d2a", "cat2", 0, 64, "d2a", 0, 32, 1),
-    ("d2b", "d2a", 0, 32, "d2b", 0, 32, 1),
-    ("u1", "up1", 0, 32, "cat1", 16, 16, 0),
-    ("d1a", "cat1", 0, 32, "d1a", 0, 16, 0),
-    ("d1b", "d1a", 0, 16, "d1b", 0, 16, 0),
-]
-# buffer channels and level
-BUFFERS = {"in0": (16, 0), "e1a": (16, 0), "cat1": (32, 0), "p1": (16, 1), "e2a": (32, 1), "cat2": (64, 1),
-           "p2": (32, 2), "e3a": (64, 2), "cat3": (128, 2), "p3": (64, 3), "e4a": (128, 3), "e4b": (128, 3),
-           "up3": (128, 2), "d3a": (64, 2), "d3b": (64, 2), "up2": (64, 1), "d2a": (32, 1), "d2b": (32, 1),
-           "up1": (32, 0), "d1a": (16, 0), "d1b": (16, 0)}
 N_FEATURES = 2
 
 _nn = None
@@ -73,11 +50,34 @@ def _lib():
             "pfnn_adam": [vp, vp, vp, vp, vp, ll, f, f, f, f, i, vp],
             "pfnn_status": [C.POINTER(i)],
             "pfnn_test_withhold_stage": [i, ll],
+            "pfnn_net_create": [C.c_ulonglong, vp, C.POINTER(vp)],
+            "pfnn_net_destroy": [vp],
+            "pfnn_net_param_shape": [i, C.POINTER(i), C.POINTER(i)],
+            "pfnn_net_set_params": [vp, i, vp, vp],
+            "pfnn_net_get_params": [vp, i, vp, vp],
+            "pfnn_net_get_grads": [vp, i, vp, vp],
+            "pfnn_net_forward": [vp, vp, vp, i, i, vp, vp],
+            "pfnn_net_infer": [vp, vp, vp, i, i, vp],
+            "pfnn_net_loss": [vp, C.POINTER(d)],
+            "pfnn_net_backward": [vp],
+            "pfnn_net_adam_step": [vp, f, f, f, f],
+            "pfnn_seed_connect": [vp, vp, vp, i, i, i, d, i, vp, vp, vp, C.POINTER(ll)],
+            "pfnn_net_layer": [i, C.POINTER(i)],
+            "pfnn_net_buffer": [i, C.POINTER(i), C.POINTER(i)],
+            "pfnn_net_read_buffer": [vp, i, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
             fn.argtypes = args
             fn.restype = C.c_int
+        lib.pfnn_net_params.argtypes = []
+        lib.pfnn_net_params.restype = C.c_int
+        lib.pfnn_net_buffers.argtypes = []
+        lib.pfnn_net_buffers.restype = C.c_int
+        lib.pfnn_net_param_name.argtypes = [i]
+        lib.pfnn_net_param_name.restype = C.c_char_p
+        lib.pfnn_net_last_error.argtypes = [vp]
+        lib.pfnn_net_last_error.restype = C.c_char_p
         _nn = lib
     return _nn
 
@@ -101,150 +101,120 @@ def check_device():
 
 
 class UNet:
-    """Parameters (FP32 master + BF16 working copies), gradients, Adam moments, and the kernels' calls."""
+    """Handle of the library's encoder-decoder (pfnn_net in include/pfnn.h): parameters, gradients, Adam
+    moments and activations live in the library; this class only marshals arguments."""
 
     def __init__(self, seed=0, device="cuda"):
         import torch
         self.torch = torch
         self.dev = device
-        g = np.random.default_rng(seed)
-        self.params = {}
-        for (name, _, _, cin, _, _, cout, _) in LAYERS:
-            std = math.sqrt(2.0 / (27 * cin))      # He initialisation for ReLU layers
-            w = torch.from_numpy((g.standard_normal((27, cout, cin)) * std).astype(np.float32)).to(device)
-            self.params[name] = self._param(w, torch.zeros(cout, device=device))
-        hw = torch.from_numpy((g.standard_normal(16) * math.sqrt(1.0 / 16)).astype(np.float32)).to(device)
-        self.head = self._param(hw, torch.zeros(1, device=device))
-        self.step_count = 0
         self.stream = torch.cuda.current_stream().cuda_stream
+        out = C.c_void_p()
+        _ck(_lib().pfnn_net_create(int(seed), C.c_void_p(self.stream), C.byref(out)), "pfnn_net_create")
+        self.handle = out
+        self.names = [_lib().pfnn_net_param_name(q).decode() for q in range(_lib().pfnn_net_params())]
+        self._prob = None
 
-    def _param(self, w, b):
-        t = self.torch
-        return {"w": w.contiguous(), "b": b.contiguous(), "wb": w.to(t.bfloat16).contiguous(),
-                "wt": t.empty((w.shape[0], w.shape[2], w.shape[1]) if w.dim() == 3 else w.shape, dtype=t.bfloat16,
-                              device=self.dev) if w.dim() == 3 else None,
-                "gw": t.zeros_like(w), "gb": t.zeros_like(b), "mw": t.zeros_like(w), "vw": t.zeros_like(w),
-                "mb": t.zeros_like(b), "vb": t.zeros_like(b)}
+    def _ck(self, st, what):
+        if st != 0:
+            msg = _lib().pfnn_net_last_error(self.handle)
+            raise _pf.PfError(st, f"{what}: {msg.decode() if msg else ''}")
 
-    # ---------------------------------------------------------------- buffers
-    def _buffers(self, n, S):
-        t = self.torch
-        key = (n, S)
-        if getattr(self, "_bkey", None) == key:
-            return
-        self._bkey = key
-        self.n, self.S = n, S
-        self.act, self.grad = {}, {}
-        for name, (c, lev) in BUFFERS.items():
-            s = S >> lev
-            self.act[name] = t.zeros((n * s ** 3, c), dtype=t.bfloat16, device=self.dev)
-            self.grad[name] = t.zeros((n * s ** 3, c), dtype=t.float32, device=self.dev)
-        nmax = n * S ** 3 * 128
-        self.dz_f = t.empty(nmax, dtype=t.float32, device=self.dev)
-        self.dz_b = t.empty(nmax, dtype=t.bfloat16, device=self.dev)
-        self.logit_grad = t.empty(n * S ** 3, dtype=t.float32, device=self.dev)
-        self.prob = t.empty(n * S ** 3, dtype=t.float32, device=self.dev)
-        self.loss = t.zeros(1, dtype=t.float64, device=self.dev)
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib().pfnn_net_destroy(self.handle)
+            self.handle = None
 
-    def _dims(self, lev):
-        s = self.S >> lev
-        return self.n, s, s, s
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
-    # ---------------------------------------------------------------- forward
+    def shape(self, name):
+        q = self.names.index(name)
+        ci, co = C.c_int(), C.c_int()
+        _ck(_lib().pfnn_net_param_shape(q, C.byref(ci), C.byref(co)), "shape")
+        return (27, co.value, ci.value) if name != "head" else (16,), (co.value,)
+
+    def get_params(self, name):
+        """(weights, biases) as float32 numpy arrays ([27][cout][cin] for a convolution, [16] for the head)."""
+        ws, bs = self.shape(name)
+        w, b = np.empty(ws, np.float32), np.empty(bs, np.float32)
+        self._ck(_lib().pfnn_net_get_params(self.handle, self.names.index(name), w.ctypes.data, b.ctypes.data), name)
+        return w, b
+
+    def set_params(self, name, w, b):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        b = np.ascontiguousarray(b, dtype=np.float32)
+        self._ck(_lib().pfnn_net_set_params(self.handle, self.names.index(name), w.ctypes.data, b.ctypes.data), name)
+
+    def get_grads(self, name):
+        ws, bs = self.shape(name)
+        w, b = np.empty(ws, np.float32), np.empty(bs, np.float32)
+        self._ck(_lib().pfnn_net_get_grads(self.handle, self.names.index(name), w.ctypes.data, b.ctypes.data), name)
+        return w, b
+
     def forward(self, G, feat, target=None):
         """G: fp32 (n * S^3,) glass field; feat: fp32 (n, N_FEATURES); returns probabilities (n * S^3,)."""
         t = self.torch
         n = feat.shape[0]
         S = round((G.numel() // n) ** (1 / 3))
         assert n * S ** 3 == G.numel() and S % 8 == 0, "grid side must be a multiple of 8"
-        self._buffers(n, S)
-        L = _lib()
-        st = self.stream
-        _ck(L.pfnn_pack_input(_p(G), _p(feat), N_FEATURES, S ** 3, n * S ** 3, _p(self.act["in0"]), st), "pack")
-        A = self.act
-        for (name, src, soff, cin, dst, doff, cout, lev) in LAYERS:
-            if name == "e2a":
-                self._pool("cat1", 0, 16, "p1", 0)
-            elif name == "e3a":
-                self._pool("cat2", 1, 32, "p2", 0)
-            elif name == "e4a":
-                self._pool("cat3", 2, 64, "p3", 0)
-            elif name == "u3":
-                _ck(L.pfnn_upsample(_p(A["e4b"]), 128, _p(A["up3"]), 128, 0, *self._dims(2), st), "up")
-            elif name == "u2":
-                _ck(L.pfnn_upsample(_p(A["d3b"]), 64, _p(A["up2"]), 64, 0, *self._dims(1), st), "up")
-            elif name == "u1":
-                _ck(L.pfnn_upsample(_p(A["d2b"]), 32, _p(A["up1"]), 32, 0, *self._dims(0), st), "up")
-            P = self.params[name]
-            ldx, ldy = BUFFERS[src][0], BUFFERS[dst][0]
-            _ck(L.pfnn_conv3d(_p(A[src]), ldx, soff, _p(P["wb"]), cin, cout, _p(P["b"]), 1, 0, _p(A[dst]), None, ldy,
-                              doff, 0, *self._dims(lev), st), name)
-        self.loss.zero_()
-        _ck(L.pfnn_head_forward(_p(A["d1b"]), 16, _p(self.head["w"]), _p(self.head["b"]), _p(target), n * S ** 3,
-                                _p(self.prob), _p(self.logit_grad) if target is not None else None,
-                                _p(self.loss) if target is not None else None, st), "head")
-        return self.prob
+        if self._prob is None or self._prob.numel() != G.numel():
+            self._prob = t.empty(G.numel(), dtype=t.float32, device=self.dev)
+        self._ck(_lib().pfnn_net_forward(self.handle, _p(G), _p(feat), n, S, _p(target), _p(self._prob)), "forward")
+        self._n, self._S = n, S
+        return self._prob
 
-    def _pool(self, src, lev, c, dst, doff):
-        _ck(_lib().pfnn_avgpool(_p(self.act[src]), BUFFERS[src][0], 0, _p(self.act[dst]), BUFFERS[dst][0], doff, c,
-                                *self._dims(lev), self.stream), "pool")
-
-    # ---------------------------------------------------------------- backward
     def backward(self):
         """Gradients of the mean BCE of the last forward (with a target) into every parameter."""
-        L = _lib()
-        st = self.stream
-        A, Gr = self.act, self.grad
-        for g in Gr.values():
-            g.zero_()
-        for P in list(self.params.values()) + [self.head]:
-            P["gw"].zero_()
-            P["gb"].zero_()
-        nvox0 = self.n * self.S ** 3
-        _ck(L.pfnn_head_backward(_p(A["d1b"]), 16, _p(self.head["w"]), _p(self.logit_grad), nvox0, _p(Gr["d1b"]),
-                                 _p(self.head["gw"]), _p(self.head["gb"]), st), "head bwd")
-        for (name, src, soff, cin, dst, doff, cout, lev) in reversed(LAYERS):
-            P = self.params[name]
-            n, d, h, w = self._dims(lev)
-            nvox = n * d * h * w
-            ldy = BUFFERS[dst][0]
-            dzf = self.dz_f[: nvox * cout]
-            dzb = self.dz_b[: nvox * cout]
-            # ReLU backward on this layer's output slice
-            _ck(L.pfnn_relu_bwd_cast(_p(Gr[dst]), ldy, doff, _p(A[dst]), ldy, doff, cout, nvox, _p(dzf), _p(dzb), st),
-                "relu bwd")
-            _ck(L.pfnn_bias_grad(_p(dzf), cout, 0, cout, nvox, _p(P["gb"]), st), "bias grad")
-            _ck(L.pfnn_conv3d_wgrad(_p(dzb), cout, 0, cout, _p(A[src]), BUFFERS[src][0], soff, cin, _p(P["gw"]), n, d,
-                                    h, w, st), "wgrad")
-            if src != "in0":
-                _ck(L.pfnn_weight_transpose(_p(P["wb"]), _p(P["wt"]), cout, cin, st), "wt")
-                _ck(L.pfnn_conv3d(_p(dzb), cout, 0, _p(P["wt"]), cout, cin, None, 0, 1, None, _p(Gr[src]),
-                                  BUFFERS[src][0], soff, 1, n, d, h, w, st), "dgrad")
-            # adjoints of the data movement that produced this layer's input
-            if name == "e2a":
-                _ck(L.pfnn_avgpool_bwd(_p(Gr["p1"]), 16, _p(Gr["cat1"]), 32, 0, *self._dims(0), st), "pool bwd")
-            elif name == "e3a":
-                _ck(L.pfnn_avgpool_bwd(_p(Gr["p2"]), 32, _p(Gr["cat2"]), 64, 0, *self._dims(1), st), "pool bwd")
-            elif name == "e4a":
-                _ck(L.pfnn_avgpool_bwd(_p(Gr["p3"]), 64, _p(Gr["cat3"]), 128, 0, *self._dims(2), st), "pool bwd")
-            elif name == "u3":
-                _ck(L.pfnn_upsample_bwd(_p(Gr["up3"]), 128, 0, 128, _p(Gr["e4b"]), *self._dims(3), st), "up bwd")
-            elif name == "u2":
-                _ck(L.pfnn_upsample_bwd(_p(Gr["up2"]), 64, 0, 64, _p(Gr["d3b"]), *self._dims(2), st), "up bwd")
-            elif name == "u1":
-                _ck(L.pfnn_upsample_bwd(_p(Gr["up1"]), 32, 0, 32, _p(Gr["d2b"]), *self._dims(1), st), "up bwd")
+        self._ck(_lib().pfnn_net_backward(self.handle), "backward")
 
     def adam_step(self, lr=2e-3, b1=0.9, b2=0.999, eps=1e-8):
-        L = _lib()
-        self.step_count += 1
-        for P in list(self.params.values()) + [self.head]:
-            _ck(L.pfnn_adam(_p(P["w"]), _p(P["gw"]), _p(P["mw"]), _p(P["vw"]), _p(P["wb"]) if P["wt"] is not None else None,
-                            P["w"].numel(), lr, b1, b2, eps, self.step_count, self.stream), "adam")
-            _ck(L.pfnn_adam(_p(P["b"]), _p(P["gb"]), _p(P["mb"]), _p(P["vb"]), None, P["b"].numel(), lr, b1, b2, eps,
-                            self.step_count, self.stream), "adam")
+        self._ck(_lib().pfnn_net_adam_step(self.handle, lr, b1, b2, eps), "adam")
+
+    def layer(self, q):
+        """Wiring of convolution q (see pfnn_net_layer)."""
+        w = (C.c_int * 12)()
+        _ck(_lib().pfnn_net_layer(int(q), w), "layer")
+        keys = ("src", "soff", "cin", "dst", "doff", "cout", "lev", "pre", "pre_src", "pre_c", "pre_dst", "pre_lev")
+        return dict(zip(keys, list(w)))
+
+    def buffer(self, b):
+        """(activations, gradients) of buffer b of the last forward / backward as float64 numpy arrays
+        (n, s, s, s, channels)."""
+        c, lev = C.c_int(), C.c_int()
+        _ck(_lib().pfnn_net_buffer(int(b), C.byref(c), C.byref(lev)), "buffer")
+        s = self._S >> lev.value
+        shape = (self._n, s, s, s, c.value)
+        a = np.empty(shape, dtype=np.uint16)
+        g = np.empty(shape, dtype=np.float32)
+        self._ck(_lib().pfnn_net_read_buffer(self.handle, int(b), a.ctypes.data, g.ctypes.data), "read_buffer")
+        act = (a.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+        return act, g.astype(np.float64)
 
     def loss_value(self):
-        return float(self.loss.item())
+        v = C.c_double()
+        self._ck(_lib().pfnn_net_loss(self.handle, C.byref(v)), "loss")
+        return v.value
+
+
+def seed_connect(prob, phi_seed, G, shape, zeta, halo=3):
+    """Network output restricted to the ice region connected to the seed (device tensors; returns a
+    binary64 device tensor and the flood-fill sweeps run)."""
+    import torch
+    n = int(shape[0]) * int(shape[1]) * int(shape[2])
+    for name, t, dt in (("prob", prob, torch.float32), ("phi_seed", phi_seed, torch.float64), ("G", G, torch.float64)):
+        if not t.is_cuda or t.dtype != dt or t.numel() != n or not t.is_contiguous():
+            raise ValueError(f"{name}: contiguous {dt} CUDA tensor of {n} values required")
+    out = torch.empty(n, dtype=torch.float64, device=prob.device)
+    work = torch.empty(16 * ((n + 15) // 16) + 16, dtype=torch.uint8, device=prob.device)
+    sw = C.c_longlong()
+    _ck(_lib().pfnn_seed_connect(_p(prob), _p(phi_seed), _p(G), int(shape[0]), int(shape[1]), int(shape[2]),
+                                 float(zeta), int(halo), _p(work), _p(out),
+                                 C.c_void_p(torch.cuda.current_stream().cuda_stream), C.byref(sw)), "seed_connect")
+    return out, sw.value
 
 
 def features(dT, sigma_scale):

@@ -29,7 +29,9 @@ EXPORTS = ["pf_create_grid", "pf_destroy_grid", "pf_set_geometry", "pf_set_glass
            "pf_max_phase_rate", "pf_profile_stages", "pf_measure_peaks", "pf_unfrozen_fraction_noalloc", "pf_last_error",
            "pf_kernel_launches", "pf_set_tiles", "pf_get_tiles", "pf_autotune", "pf_batch_create",
            "pf_batch_destroy", "pf_batch_grid", "pf_batch_autotune", "pf_batch_run_to", "pf_batch_iterations",
-           "pf_batch_last_error"]
+           "pf_batch_last_error", "pf_slabs_create", "pf_slabs_destroy", "pf_slabs_grid", "pf_slabs_set_geometry",
+           "pf_slabs_set_tiles", "pf_slabs_set_state", "pf_slabs_get_state", "pf_slabs_run_to",
+           "pf_slabs_unfrozen_fraction", "pf_slabs_halo_bytes", "pf_slabs_last_error"]
 
 
 class PfError(RuntimeError):
@@ -57,11 +59,12 @@ class pf_run_stats(C.Structure):
 
 
 class pf_batch_result(C.Structure):
-    _fields_ = [("stats", pf_run_stats), ("t_eq", C.c_double), ("equilibrium", C.c_int), ("status", C.c_int)]
+    _fields_ = [("stats", pf_run_stats), ("t_eq", C.c_double), ("rate", C.c_double), ("equilibrium", C.c_int),
+                ("status", C.c_int)]
 
     def as_dict(self):
         d = self.stats.as_dict()
-        d.update(t_eq=self.t_eq, equilibrium=bool(self.equilibrium), status=self.status)
+        d.update(t_eq=self.t_eq, rate=self.rate, equilibrium=bool(self.equilibrium), status=self.status)
         return d
 
 
@@ -100,8 +103,16 @@ def load_library(path: str = LIB_PATH):
         "pf_batch_create": [i, C.POINTER(vp), C.POINTER(vp)],
         "pf_batch_destroy": [vp],
         "pf_batch_autotune": [vp, C.c_char_p],
-        "pf_batch_run_to": [vp, pd, pd, d, d, ll, C.POINTER(pf_batch_result)],
+        "pf_batch_run_to": [vp, pd, pd, d, pd, d, ll, C.POINTER(pf_batch_result)],
         "pf_unfrozen_fraction_noalloc": [vp, vp, i, i, i, vp, vp, pd, pll, pll, pd],
+        "pf_slabs_create": [i, i, i, d, i, i, i, C.POINTER(pf_params), i, vp, vp, C.POINTER(vp)],
+        "pf_slabs_destroy": [vp],
+        "pf_slabs_set_geometry": [vp, vp, ll, d],
+        "pf_slabs_set_tiles": [vp, i, i],
+        "pf_slabs_set_state": [vp, vp, vp, d, d],
+        "pf_slabs_get_state": [vp, vp, vp, pd, pd],
+        "pf_slabs_run_to": [vp, d, d, ll, C.POINTER(pf_run_stats)],
+        "pf_slabs_unfrozen_fraction": [vp, pd, pll, pll],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -117,6 +128,12 @@ def load_library(path: str = LIB_PATH):
     lib.pf_batch_iterations.restype = C.c_longlong
     lib.pf_batch_last_error.argtypes = [vp]
     lib.pf_batch_last_error.restype = C.c_char_p
+    lib.pf_slabs_grid.argtypes = [vp, i]
+    lib.pf_slabs_grid.restype = vp
+    lib.pf_slabs_halo_bytes.argtypes = [vp]
+    lib.pf_slabs_halo_bytes.restype = C.c_longlong
+    lib.pf_slabs_last_error.argtypes = [vp]
+    lib.pf_slabs_last_error.restype = C.c_char_p
     _lib = lib
     return lib
 
@@ -382,11 +399,12 @@ class Batch:
         self._check(_lib.pf_batch_autotune(self.handle, cache_path.encode() if cache_path else None))
         return [g.get_tiles() for g in self.grids]
 
-    def run_to(self, t_end, tol, max_steps, eq_window=None, eq_rel_tol=0.0):
+    def run_to(self, t_end, tol, max_steps, eq_window=None, eq_rel_tol=0.0, eq_rate=None):
         te = (C.c_double * self.n)(*[float(v) for v in t_end])
         er = None if eq_window is None else (C.c_double * self.n)(*[float(v) for v in eq_window])
+        rr = None if eq_rate is None else (C.c_double * self.n)(*[float(v) for v in eq_rate])
         res = (pf_batch_result * self.n)()
-        self._check(_lib.pf_batch_run_to(self.handle, te, er, float(eq_rel_tol), float(tol), int(max_steps), res))
+        self._check(_lib.pf_batch_run_to(self.handle, te, er, float(eq_rel_tol), rr, float(tol), int(max_steps), res))
         return [r.as_dict() for r in res]
 
     def iterations(self):
@@ -406,12 +424,85 @@ class Batch:
             pass
 
 
+class Slabs:
+    """Owning handle of a pf_slabs group: the n1 x n2 x n3 grid cut along x3 into slabs that exchange
+    their cut planes every stage and share one step control (the paper's 1-D decomposition, Sec. 2.5,
+    in one process on one GPU).  Host arrays hold the whole grid."""
+
+    def __init__(self, shape, h, model, reaction=0, precision=0, params=None, nslabs=2, planes=None, stream=None):
+        lib = load_library()
+        self.shape = tuple(int(v) for v in shape)
+        self.N = self.shape[0] * self.shape[1] * self.shape[2]
+        self.params = dict(params or _inputs.default_params())
+        self._cparams = make_params(self.params)
+        import torch
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        pl = None if planes is None else (C.c_int * (nslabs + 1))(*[int(v) for v in planes])
+        out = C.c_void_p()
+        st = lib.pf_slabs_create(self.shape[0], self.shape[1], self.shape[2], float(h), int(model), int(reaction),
+                                 int(precision), C.byref(self._cparams), int(nslabs), pl,
+                                 C.c_void_p(self.stream.cuda_stream), C.byref(out))
+        if st != PF_OK:
+            msg = lib.pf_slabs_last_error(None)
+            raise PfError(st, msg.decode() if msg else "")
+        self.handle = out
+        self.nslabs = int(nslabs)
+
+    def _check(self, st):
+        if st != PF_OK:
+            msg = _lib.pf_slabs_last_error(self.handle)
+            raise PfError(st, msg.decode() if msg else "")
+
+    def set_geometry(self, spheres, x3_cap=math.nan):
+        sp = np.ascontiguousarray(spheres, dtype=np.float64).reshape(-1, 4)
+        self._check(_lib.pf_slabs_set_geometry(self.handle, sp.ctypes.data if sp.size else None, sp.shape[0], x3_cap))
+
+    def set_tiles(self, by, zc):
+        self._check(_lib.pf_slabs_set_tiles(self.handle, int(by), int(zc)))
+
+    def set_state(self, theta, phi, t=0.0, dt=1e-3):
+        pt, k1 = _host(theta, self.N)
+        pp, k2 = _host(phi, self.N)
+        self._check(_lib.pf_slabs_set_state(self.handle, pt, pp, float(t), float(dt)))
+
+    def get_state(self):
+        th, ph = np.empty(self.N), np.empty(self.N)
+        t, dt = C.c_double(), C.c_double()
+        self._check(_lib.pf_slabs_get_state(self.handle, th.ctypes.data, ph.ctypes.data, C.byref(t), C.byref(dt)))
+        return th, ph, t.value, dt.value
+
+    def run_to(self, t_end, tol, max_steps):
+        s = pf_run_stats()
+        self._check(_lib.pf_slabs_run_to(self.handle, float(t_end), float(tol), int(max_steps), C.byref(s)))
+        return s.as_dict()
+
+    def unfrozen_fraction(self):
+        u = C.c_double()
+        ni, nw = C.c_longlong(), C.c_longlong()
+        self._check(_lib.pf_slabs_unfrozen_fraction(self.handle, C.byref(u), C.byref(ni), C.byref(nw)))
+        return {"uwc": u.value, "n_ice": ni.value, "n_water": nw.value}
+
+    def halo_bytes(self):
+        return _lib.pf_slabs_halo_bytes(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.pf_slabs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def pf_batch_create(grids):
     return Batch(grids)
 
 
-def pf_batch_run_to(b, t_end, tol, max_steps, eq_window=None, eq_rel_tol=0.0):
-    return b.run_to(t_end, tol, max_steps, eq_window, eq_rel_tol)
+def pf_batch_run_to(b, t_end, tol, max_steps, eq_window=None, eq_rel_tol=0.0, eq_rate=None):
+    return b.run_to(t_end, tol, max_steps, eq_window, eq_rel_tol, eq_rate)
 
 
 def pf_autotune(g, cache_path=None):

@@ -3,9 +3,11 @@
 generate(): equilibria of many small instances from batched binary32-field runs (the batched
             persistent solver), as training pairs (glass field, features) -> phase field.
 train():    Adam on the library's own BF16 tensor-core forward/backward kernels.
-predict():  network phase field for a (large) instance, clipped to [0, 1] and kept 0 where I_W = 0.
+predict():  network phase field for a (large) instance, kept in the ice region connected to the seed
+            (clipped to [0, 1]) and equal to the seed's phase field elsewhere.
 relax():    the plain binary64 Runge-Kutta-Merson integration from a given phase field to the
-            equilibrium test (ice count unchanged for the time a free front needs to cross 20 cells), which stays the judge of the result.
+            equilibrium test (ice count unchanged for the time a free front needs to cross 20 cells and
+            no pore interface faster than 1 % of the free-front speed), which stays the judge of the result.
 """
 from __future__ import annotations
 
@@ -18,10 +20,9 @@ from . import inputs as I
 from . import nn as NN
 from . import pf
 
-# equilibrium: the pore ice count stays within 1e-3 of the pore cells for the instance's window,
-# i.e. the unfrozen-water content is settled to 0.1 % (the accuracy asked of the results)
-EQ_REL_TOL = 1e-3
 from . import sweep
+
+EQ_REL_TOL = sweep.EQ_REL_TOL
 
 
 def generate(instances, max_steps=4000, batch=128, t_end_factor=50.0):
@@ -35,7 +36,8 @@ def generate(instances, max_steps=4000, batch=128, t_end_factor=50.0):
         grids = [sweep._grid(inst, I.PREC_FP32, stream) for inst in chunk]
         b = pf.Batch(grids)
         res = b.run_to([i.t_end * t_end_factor for i in chunk], 1e-6, max_steps,
-                       eq_window=[i.eq_window for i in chunk], eq_rel_tol=EQ_REL_TOL)
+                       eq_window=[i.eq_window for i in chunk], eq_rel_tol=EQ_REL_TOL,
+                       eq_rate=[sweep.eq_rate(i) for i in chunk])
         for inst, g, r in zip(chunk, grids, res):
             Gs.append(torch.from_numpy(g.get_glass().astype(np.float32)))
             Ps.append(torch.from_numpy(g.get_state()[1].astype(np.float32)))
@@ -68,18 +70,18 @@ def train(G, feat, P, steps=600, batch=4, lr=2e-3, seed=0, log_every=0):
     return net, hist
 
 
-def predict(net, inst, G):
-    """Network phase field for one instance (G: host glass field), as a host float64 array."""
+def predict(net, inst, G, halo=3):
+    """Network phase field for one instance (G: host glass field), as a host float64 array: the network's
+    output kept in the ice region connected to the seed (the micro model has no nucleation), the seed's
+    phase field elsewhere and in the cells whose water indicator is zero (they never change)."""
     import torch
     Gd = torch.from_numpy(G.astype(np.float32)).cuda()
     feat = torch.tensor([NN.features(inst.dT, inst.sigma_scale)], dtype=torch.float32, device="cuda")
     prob = net.forward(Gd, feat)
     NN.check_device()
-    phi = prob.double().cpu().numpy()
-    # cells with I_W = 0 never change (eq. water-indicator): keep their initial value
-    frozen = (1.0 - inst.params["zeta"] * G) <= 0.0
-    phi[frozen] = inst.phi0[frozen]
-    return phi
+    phi, _ = NN.seed_connect(prob, torch.from_numpy(np.ascontiguousarray(inst.phi0)).cuda(),
+                             torch.from_numpy(np.ascontiguousarray(G)).cuda(), inst.shape, inst.params["zeta"], halo)
+    return phi.cpu().numpy()
 
 
 def relax(inst, phi_init, max_steps=20000, precision=I.PREC_FP64, t_end_factor=50.0):
@@ -94,7 +96,7 @@ def relax(inst, phi_init, max_steps=20000, precision=I.PREC_FP64, t_end_factor=5
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     r = b.run_to([inst.t_end * t_end_factor], 1e-6, max_steps, eq_window=[inst.eq_window],
-                       eq_rel_tol=EQ_REL_TOL)[0]
+                 eq_rel_tol=EQ_REL_TOL, eq_rate=[sweep.eq_rate(inst)])[0]
     wall = time.perf_counter() - t0
     phi = g.get_state()[1]
     r["uwc"] = g.unfrozen_fraction()["uwc"]
