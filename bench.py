@@ -604,6 +604,9 @@ def run_warmstart(args, rank, world):
                               "inference_s": t_inf, "equilibrium": warm["equilibrium"], "t_eq": warm["t_eq"],
                               "uwc": warm["uwc"]},
                      "max_abs_dphi_warm_vs_cold": float(np.max(np.abs(phi_w - phi_c))),
+                     "max_abs_dphi_pore_bulk": float(np.max(np.abs(phi_w - phi_c)[
+                         (1.0 - inst.params["zeta"] * Gt) > 0.5])),
+                     "cells_off_by_1e-3": float(np.mean(np.abs(phi_w - phi_c) > 1e-3)),
                      "max_abs_dphi_prediction_vs_cold": float(np.max(np.abs(phi_pred - phi_c))),
                      "uwc_rel_diff": abs(warm["uwc"] - cold["uwc"]) / max(abs(cold["uwc"]), 1e-12)})
     from paper_2401_01672_gb300 import sweep as SW
@@ -632,6 +635,30 @@ def run_warmstart(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_stages(args, rank, world):
+    """Stage kernels only, for profiler captures: the bead workload at --size (default 192) from its
+    mid-front state, one precision form (--form), the tile shape given (--tiles, default 4 x 12) or the
+    autotuner's, one attempt of warm-up then --steps attempts launched one kernel at a time
+    (pf_profile_stages: stages 1..5 then the controller per attempt).  Prints the stage times."""
+    import torch
+    from paper_2401_01672_gb300 import pf
+    if rank != 0:
+        return
+    w = make_workload("full256", args.size or 192)
+    prec = I.PREC_FP32 if args.form == "f32" else I.PREC_FP64
+    g = pf.Grid(w.shape, w.h, w.model, w.reaction, prec, w.params)
+    g.set_geometry(w.spheres, w.x3_cap)
+    mid = I.midfront_state(w, g.get_glass())
+    g.set_state(mid[0], mid[1], 0.0, 0.01)
+    set_tiles(g, args.tiles or (4, 12))
+    g.profile_stages(1)
+    prof = g.profile_stages(args.steps)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": f"stages_{args.form}_{w.shape[0]}", "tiles_by_zc": list(g.get_tiles()),
+                      "attempts": args.steps, "stage_ms": prof}), flush=True)
+    g.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -643,11 +670,12 @@ def main():
     ap.add_argument("--tiles", type=int, nargs=2, metavar=("BY", "ZC"), default=None,
                     help="fixed tile shape (block height, z chunk) instead of the autotuner's choice")
     ap.add_argument("--workload", default="full256",
-                    choices=["full256", "full512", "sweep48", "warmstart", "macro", "uwc", "conv"],
+                    choices=["full256", "full512", "sweep48", "warmstart", "macro", "uwc", "conv", "stages"],
                     help="full256: the binary64 bead workload (default); full512: the 512^3 lognormal packing, both "
                          "forms, with the crop error study; sweep48: the 48-instance micro-scale "
                          "sweep, batched binary32 persistent run vs the plain binary64 method")
     ap.add_argument("--no-crop-study", action="store_true", help="full512: skip the 128^3 crop error study")
+    ap.add_argument("--form", default="f64", choices=["f64", "f32"], help="stages: precision form")
     ap.add_argument("--max-steps", type=int, default=600, help="sweep48, uwc: attempt cap per instance")
     ap.add_argument("--macro-n3", type=int, default=100, help="macro: cells along the vessel height (100/200/400)")
     ap.add_argument("--macro-cap", type=int, default=1_500_000, help="macro: attempt cap per run")
@@ -691,6 +719,9 @@ def main():
         return
     if args.workload == "conv":
         run_conv(args, rank, world)
+        return
+    if args.workload == "stages":
+        run_stages(args, rank, world)
         return
     dist = None
     if world > 1:

@@ -97,14 +97,16 @@ pf_status pfnn_adam(float* p, const float* g, float* m, float* v, void* p_bf16, 
 /* Warm-start constraint (the micro-scale model of Sec. 2.4 has no nucleation term: ice only exists where
  * it grew from the seed through the pore space).  From the network output prob (device fp32, n1 n2 n3,
  * x fastest), the seed phase field phi_seed and the glass field G (device binary64): the cells that may
- * carry ice are those with prob > 1/2 and a water indicator 1 - zeta G above zero; the ones connected to
- * the seed (phi_seed > 1/2) through face neighbours, grown by `halo` cells (0..64) to keep the diffuse
- * interface, take max(prob clamped to [0, 1], phi_seed); every other cell takes phi_seed (cells with a zero water
- * indicator never change).  work: caller-owned device scratch of at least 16 * ceil(n / 16) + 4 bytes.
- * The flood fill sweeps in place until a sweep reaches no new cell (checked every 16 sweeps; bounded by
- * the cell count); *sweeps (may be NULL) receives the sweeps run.  Synchronises `stream`. */
+ * carry ice are those with prob > 1/2 and a water indicator 1 - zeta G above zero, eroded by `erode` cells
+ * (0..64; throats narrower than about twice that are cut); the ones connected to the seed (phi_seed > 1/2)
+ * through face neighbours, grown back by `erode` cells inside the predicted ice and by `halo` cells (0..64)
+ * beyond it to keep the diffuse interface, take max(prob clamped to [0, 1], phi_seed); every other cell
+ * takes phi_seed (cells with a zero water indicator never change).  work: caller-owned device scratch of
+ * at least 16 * ceil(n / 16) + 4 bytes.  The flood fill sweeps in place until a sweep reaches no new cell
+ * (checked every 16 sweeps; bounded by the cell count); *sweeps (may be NULL) receives the sweeps run.
+ * Synchronises `stream`. */
 pf_status pfnn_seed_connect(const float* prob, const double* phi_seed, const double* G, int n1, int n2, int n3,
-                            double zeta, int halo, unsigned char* work, double* phi_out, void* stream,
+                            double zeta, int erode, int halo, unsigned char* work, double* phi_out, void* stream,
                             long long* sweeps);
 
 /* ---- The warm-start network as one object (pfnn_net): the 3D convolutional encoder-decoder of 4 levels

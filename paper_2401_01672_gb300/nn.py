@@ -61,7 +61,7 @@ def _lib():
             "pfnn_net_loss": [vp, C.POINTER(d)],
             "pfnn_net_backward": [vp],
             "pfnn_net_adam_step": [vp, f, f, f, f],
-            "pfnn_seed_connect": [vp, vp, vp, i, i, i, d, i, vp, vp, vp, C.POINTER(ll)],
+            "pfnn_seed_connect": [vp, vp, vp, i, i, i, d, i, i, vp, vp, vp, C.POINTER(ll)],
             "pfnn_net_layer": [i, C.POINTER(i)],
             "pfnn_net_buffer": [i, C.POINTER(i), C.POINTER(i)],
             "pfnn_net_read_buffer": [vp, i, vp, vp],
@@ -200,7 +200,7 @@ class UNet:
         return v.value
 
 
-def seed_connect(prob, phi_seed, G, shape, zeta, halo=3):
+def seed_connect(prob, phi_seed, G, shape, zeta, halo=3, erode=0):
     """Network output restricted to the ice region connected to the seed (device tensors; returns a
     binary64 device tensor and the flood-fill sweeps run)."""
     import torch
@@ -212,7 +212,7 @@ def seed_connect(prob, phi_seed, G, shape, zeta, halo=3):
     work = torch.empty(16 * ((n + 15) // 16) + 16, dtype=torch.uint8, device=prob.device)
     sw = C.c_longlong()
     _ck(_lib().pfnn_seed_connect(_p(prob), _p(phi_seed), _p(G), int(shape[0]), int(shape[1]), int(shape[2]),
-                                 float(zeta), int(halo), _p(work), _p(out),
+                                 float(zeta), int(erode), int(halo), _p(work), _p(out),
                                  C.c_void_p(torch.cuda.current_stream().cuda_stream), C.byref(sw)), "seed_connect")
     return out, sw.value
 

@@ -18,9 +18,10 @@ from . import pf
 # equilibrium: the pore ice count stays within 1e-3 of the pore cells for the instance's window,
 # i.e. the unfrozen-water content is settled to 0.1 % (the accuracy asked of the results), and no pore
 # interface moves faster than EQ_SPEED_FRAC times the free-front speed mu dT (residual test on
-# |dphi/dt|: a tanh interface of width xi moving at v has max |dphi/dt| = v / (4 xi), Sec. 2.2)
+# |dphi/dt|: a tanh interface of width xi moving at v has max |dphi/dt| = v / (4 xi), Sec. 2.2).
+# Measured on 64^3 instances: 1e-3 costs the plain run from the seed about 3 % more attempts than 1e-2.
 EQ_REL_TOL = 1e-3
-EQ_SPEED_FRAC = 1e-2
+EQ_SPEED_FRAC = 1e-3
 
 
 def eq_rate(inst, frac=None):
@@ -88,6 +89,11 @@ def run_plain(instances, tol=1e-6, max_steps=1000, precision=I.PREC_FP64, keep_p
 # accuracy bars of a result against the plain binary64 method: max |dphi| and the unfrozen-water fraction
 BAR_DPHI = 1e-3
 BAR_UWC_REL = 5e-3
+
+
+def pore_bulk(G, zeta):
+    """Cells whose water indicator is above 1/2 (the pore bulk of the equilibrium test)."""
+    return (1.0 - zeta * np.asarray(G)) > 0.5
 
 
 def compare(batched, plain):

@@ -70,7 +70,7 @@ def train(G, feat, P, steps=600, batch=4, lr=2e-3, seed=0, log_every=0):
     return net, hist
 
 
-def predict(net, inst, G, halo=3):
+def predict(net, inst, G, halo=3, erode=0):
     """Network phase field for one instance (G: host glass field), as a host float64 array: the network's
     output kept in the ice region connected to the seed (the micro model has no nucleation), the seed's
     phase field elsewhere and in the cells whose water indicator is zero (they never change)."""
@@ -80,13 +80,15 @@ def predict(net, inst, G, halo=3):
     prob = net.forward(Gd, feat)
     NN.check_device()
     phi, _ = NN.seed_connect(prob, torch.from_numpy(np.ascontiguousarray(inst.phi0)).cuda(),
-                             torch.from_numpy(np.ascontiguousarray(G)).cuda(), inst.shape, inst.params["zeta"], halo)
+                             torch.from_numpy(np.ascontiguousarray(G)).cuda(), inst.shape, inst.params["zeta"], halo,
+                             erode)
     return phi.cpu().numpy()
 
 
-def relax(inst, phi_init, max_steps=20000, precision=I.PREC_FP64, t_end_factor=50.0):
+def relax(inst, phi_init, max_steps=20000, precision=I.PREC_FP64, t_end_factor=50.0, eq_frac=None):
     """Binary64 RKM from phi_init until the equilibrium test holds (the end time is only a backstop,
-    t_end_factor times the instance's nominal t_end); returns (result, phi, wall seconds, G)."""
+    t_end_factor times the instance's nominal t_end; eq_frac overrides the residual test's fraction of the
+    free-front speed); returns (result, phi, wall seconds, G)."""
     import torch
     stream = torch.cuda.Stream()
     g = pf.Grid(inst.shape, inst.h, I.MODEL_MICRO, I.REACT_SIGMAP1P, precision, inst.params, stream=stream)
@@ -96,7 +98,7 @@ def relax(inst, phi_init, max_steps=20000, precision=I.PREC_FP64, t_end_factor=5
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     r = b.run_to([inst.t_end * t_end_factor], 1e-6, max_steps, eq_window=[inst.eq_window],
-                 eq_rel_tol=EQ_REL_TOL, eq_rate=[sweep.eq_rate(inst)])[0]
+                 eq_rel_tol=EQ_REL_TOL, eq_rate=[sweep.eq_rate(inst, eq_frac)])[0]
     wall = time.perf_counter() - t0
     phi = g.get_state()[1]
     r["uwc"] = g.unfrozen_fraction()["uwc"]

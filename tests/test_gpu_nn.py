@@ -344,7 +344,8 @@ def test_unet_layer_by_layer_against_oracle(env):
             assert np.array_equal(act[w["pre_dst"]][..., :w["pre_c"]], O.upsample(act[w["pre_src"]][..., :w["pre_c"]]))
         yr = bf16r(np.maximum(O.conv3d(x, Wb, bias.astype(np.float64)), 0))
         diff = np.abs(y - yr)
-        step = np.abs(yr) * 2.0 ** -7 + 1e-30
+        # one BF16 step of the value, plus the FP32 accumulation's noise on sums that cancel to near zero
+        step = np.abs(yr) * 2.0 ** -7 + np.max(np.abs(yr)) * 2.0 ** -14
         assert np.all(diff <= step), (name, float(np.max(diff / step)))
         frac = float(np.mean(diff > 0))
         assert frac <= 0.02, (name, frac)
