@@ -95,7 +95,7 @@ typedef struct pf_run_stats {
 } pf_run_stats;
 
 /* Create a grid and allocate its device buffers.
- * n1, n2, n3 >= 1; h > 0 [m]; model/reaction/precision from the enums above; p copied;
+ * n1, n2, n3 >= 1 with n1 n2 (n3 + 2) < 2^31 (cells are indexed with 32-bit integers); h > 0 [m]; model/reaction/precision from the enums above; p copied;
  * stream: a cudaStream_t (NULL = legacy default stream).  Geometry defaults to G = 0
  * (all water), state to theta = 0, phi = 0, t = 0, dt = dt_max (or 1e-3 s when dt_max is inf).
  * Sec. 2.5: uniform N1 x N2 x N3 finite-volume mesh. */

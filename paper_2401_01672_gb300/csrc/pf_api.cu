@@ -542,7 +542,8 @@ static pf_status create_impl(int n1, int n2, int n3, double h, int model, int re
     *out = nullptr;
     if (!p) return fail(nullptr, PF_E_INVALID, "params is NULL");
     if (n1 < 1 || n2 < 1 || n3 < 1) return fail(nullptr, PF_E_INVALID, "grid sizes must be >= 1");
-    if ((long long)n1 * n2 * n3 > (1LL << 36)) return fail(nullptr, PF_E_INVALID, "grid too large");
+    // the stage kernels index cells with 32-bit integers (ghost planes of a slab included)
+    if ((long long)n1 * n2 * ((long long)n3 + 2) >= (1LL << 31)) return fail(nullptr, PF_E_INVALID, "grid too large");
     if (!(h > 0.0)) return fail(nullptr, PF_E_INVALID, "h must be > 0");
     if (model < 0 || model > 2) return fail(nullptr, PF_E_INVALID, "unknown model");
     if (reaction < 0 || reaction > 1) return fail(nullptr, PF_E_INVALID, "unknown reaction");

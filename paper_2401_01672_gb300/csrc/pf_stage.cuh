@@ -222,8 +222,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
     const int kb = bzi * a.zc;
     const int ke = min(kb + a.zc, n3);
     const bool inside = (i < n1) && (j < n2);
-    const long long plane = (long long)n1 * n2;
-    const long long ooff = (long long)min(j, n2 - 1) * n1 + min(i, n1 - 1);
+    // 32-bit cell indices (grids are limited to fewer than 2^31 cells, ghost planes included, at creation)
+    const int plane = n1 * n2;
+    const int ooff = min(j, n2 - 1) * n1 + min(i, n1 - 1);
 
     // one halo cell per thread for the first 2 TX + 2 BY threads: y rows, then x columns
     const int tid = ty * TX + tx;
@@ -239,7 +240,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
         hy = r % BY;
         hx = (r < BY) ? -1 : TX;
     }
-    const long long hoff = (long long)min(max(j0 + hy, 0), n2 - 1) * n1 + min(max(i0 + hx, 0), n1 - 1);
+    const int hoff = min(max(j0 + hy, 0), n2 - 1) * n1 + min(max(i0 + hx, 0), n1 - 1);
 
     const TIN* in_th = nullptr;
     const TIN* in_ph = nullptr;
@@ -263,16 +264,22 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
     __shared__ T s_ph[3][SY][SX];
     __shared__ T s_lam[HAS_TH ? 3 : 1][SY][SX];
 
+    // the per-cell coefficient arrays (64-bit offsets between arrays, computed once)
     const double* __restrict__ St = a.statics;
+    const double* __restrict__ St_B = St + a.ncell;
+    const double* __restrict__ St_W = St + 2 * a.ncell;
+    const double* __restrict__ St_C = St + 3 * a.ncell;
+    const double* __restrict__ St_D = St + 6 * a.ncell;
+    const double* __restrict__ St_I = St + 8 * a.ncell;
     const long long NC = a.ncell;
     // raw loads of one cell of plane kk (clamped: mirror ghosts); G holds A_lam and B B_lam when STATIC
     // (theta and phi stay in the input type until `cvt`, so that a conversion does not wait for its
     // load where the load is issued)
-    auto fetch = [&](int kk, long long off, TIN& th, TIN& ph, T& G, T& B) {
-        const long long id = (long long)min(max(kk, a.cf.zlo), a.cf.zhi) * plane + off;
+    auto fetch = [&](int kk, int off, TIN& th, TIN& ph, T& G, T& B) {
+        const int id = min(max(kk, a.cf.zlo), a.cf.zhi) * plane + off;
         if constexpr (STATIC) {
             G = T(St[id]);
-            B = T(St[NC + id]);
+            B = T(St_B[id]);
         } else {
             G = Gf[id];
             B = T(0);
@@ -288,7 +295,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
         if constexpr (HAS_PH) ph = to_T<T>(rph);
         else ph = T(0);
     };
-    auto fetch_cvt = [&](int kk, long long off, T& th, T& ph, T& G, T& B) {
+    auto fetch_cvt = [&](int kk, int off, T& th, T& ph, T& G, T& B) {
         TIN rth, rph;
         fetch(kk, off, rth, rph, G, B);
         cvt(rth, rph, th, ph);
@@ -311,6 +318,35 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
         s_ph[b][y][x] = ph;
     };
 
+    // Allen-Cahn rate of one cell from phi, its six neighbours, theta and W = 2 I_W / (alpha xi^2) > 0
+    // (eqs. Allen-Cahn-equation, reaction-term-GradP, reaction-term-SigmaP1-P, Sigma-limiter)
+    auto ac_rate = [&](T pc, T pxm, T pxp, T pym, T pyp, T pzm, T pzp, T th, T W) -> T {
+        const T lsum = ((pxm + pxp) + (pym + pyp)) + (pzm + pzp);
+        const T lap = FMA(T(-6), pc, lsum);
+        const T om = T(1) - pc;
+        const T q = pc * om;
+        T inner = pc - T(0.5);
+        T fh;
+        if constexpr (RX == R_GRADP) {
+            const T gx = pxp - pxm, gy = pyp - pym, gz = pzp - pzm;
+            const T gn = dsqrt(FMA(gx, gx, FMA(gy, gy, gz * gz)));
+            fh = FMA(q, inner, K.kgrad * gn * (-th));          // eq. (reaction-term-GradP) / 2
+        } else {
+            if (!le_nonneg(pc, K.eps0) && !le_nonneg(om, K.eps0)) {
+                const T S = sigma_lim(pc, K) * sigma_lim(om, K);
+                inner = FMA(K.ksig * S, -th, inner);            // eq. (reaction-term-SigmaP1-P) / 2
+            }
+            fh = q * inner;
+        }
+        return W * FMA(K.klap, lap, fh);
+    };
+    // binary64 (full and micro models): the Allen-Cahn arithmetic runs on compacted slots (not for the
+    // 16-row blocks, whose planes already fill most of the 48 KiB of static shared memory)
+    constexpr bool COMPACT = !F32 && !TEMP && BY <= 8;
+    __shared__ int s_wcnt[BY];
+    __shared__ int s_slot_xy[COMPACT ? TX * BY : 1];
+    __shared__ T s_slot[COMPACT ? 4 : 1][COMPACT ? TX * BY : 1];
+
     // Dirichlet faces of this column (x and y faces are fixed along the march)
     const int dmask = a.cf.dirichlet;
     int nd_xy = 0;
@@ -327,7 +363,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
     T n_k1t = T(0), n_k1p = T(0), n_k3t = T(0), n_k3p = T(0), n_uat = T(0), n_uap = T(0);
     if constexpr (PF) {
         if (inside && kb < ke) {
-            const long long q = (long long)kb * plane + (long long)j * n1 + i;
+            const int q = kb * plane + j * n1 + i;
             if constexpr (HAS_TH) n_k1t = a.k1_th[q];
             if constexpr (HAS_PH) n_k1p = a.k1_ph[q];
             if constexpr (STAGE == 3) {
@@ -380,7 +416,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
         fetch(k + 2, ooff, rth, rph, rG, rB);
         if (hal) fetch(k + 2, hoff, qth, qph, qG, qB);
 
-        const long long id = (long long)k * plane + (long long)j * n1 + i;
+        const int id = k * plane + j * n1 + i;
         // phase field of the lateral neighbours (Laplacian, gradient) and the bulk test
         // (binary64 only: its integer test is free next to the binary64 arithmetic it can save, while
         // the binary32 kernels are bound by memory and instruction issue, where the test costs more)
@@ -400,7 +436,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
             // take the operands loaded during the previous plane, then load those of plane k+1
             k1t = n_k1t; k1p = n_k1p; k3t = n_k3t; k3p = n_k3p; ua_t = n_uat; ua_p = n_uap;
             if (inside && k + 1 < ke) {
-                const long long q = id + plane;
+                const int q = id + plane;
                 if constexpr (HAS_TH) n_k1t = a.k1_th[q];
                 if constexpr (HAS_PH) n_k1p = a.k1_ph[q];
                 if constexpr (STAGE == 3) {
@@ -435,19 +471,19 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
             }
             if constexpr (STATIC) {
                 // a bulk cell needs only 1/(rho c) at its phi; stage 1 also counts the pore cells (W)
-                if (STAGE == 1 || !bulk) sW = St[2 * NC + id];
+                if (STAGE == 1 || !bulk) sW = St_W[id];
                 if (bulk) {
-                    sIR = St[(is_one(phc) ? 9 : 8) * NC + id];
+                    sIR = St_I[(is_one(phc) ? NC : 0) + id];
                 } else {
-                    sC0 = St[3 * NC + id]; sC1 = St[4 * NC + id]; sC2 = St[5 * NC + id];
-                    sD0 = St[6 * NC + id]; sD1 = St[7 * NC + id];
+                    sC0 = St_C[id]; sC1 = St_C[NC + id]; sC2 = St_C[2 * NC + id];
+                    sD0 = St_D[id]; sD1 = St_D[NC + id];
                 }
             }
         }
 
+        // ---- heat flux divergence (eq. heat-equation), per-face conductivity, lambda pre-scaled by 1/(2h^2)
+        T div = T(0);
         if (inside) {
-            // ---- heat flux divergence (eq. heat-equation), per-face conductivity, lambda pre-scaled by 1/(2h^2)
-            T div = T(0);
             if constexpr (MODEL != M_MICRO) {
                 const T t_xm = s_th[b][ty + 1][tx], t_xp = s_th[b][ty + 1][tx + 2];
                 const T t_ym = s_th[b][ty][tx + 1], t_yp = s_th[b][ty + 2][tx + 1];
@@ -478,39 +514,60 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
                     if (nd) div = FMA(T(4 * nd) * lamc, th_b - thc, div);
                 }
             }
-            // ---- Allen-Cahn rate (eq. Allen-Cahn-equation): dphi = W (klap lap + f/2), W = 2 I_W/(alpha xi^2)
-            T dph = T(0);
-            if constexpr (!TEMP) {
-                T W = T(0);
-                if (!bulk) {  // bulk cells: dphi = 0 without arithmetic
-                    if constexpr (STATIC) W = sW;
-                    else W = FMA(K.wb, Gc, K.wa);
-                }
-                if (positive(W)) {
-                    if constexpr (F32) {
-                        p_xm = s_ph[b][ty + 1][tx]; p_xp = s_ph[b][ty + 1][tx + 2];
-                        p_ym = s_ph[b][ty][tx + 1]; p_yp = s_ph[b][ty + 2][tx + 1];
-                    }
-                    const T lsum = ((p_xm + p_xp) + (p_ym + p_yp)) + (phm + php);
-                    const T lap = FMA(T(-6), phc, lsum);
-                    const T om = T(1) - phc;
-                    const T q = phc * om;
-                    T inner = phc - T(0.5);
-                    T fh;
-                    if constexpr (RX == R_GRADP) {
-                        const T gx = p_xp - p_xm, gy = p_yp - p_ym, gz = php - phm;
-                        const T gn = dsqrt(FMA(gx, gx, FMA(gy, gy, gz * gz)));
-                        fh = FMA(q, inner, K.kgrad * gn * (-thc));          // eq. (reaction-term-GradP) / 2
-                    } else {
-                        if (!le_nonneg(phc, K.eps0) && !le_nonneg(om, K.eps0)) {
-                            const T S = sigma_lim(phc, K) * sigma_lim(om, K);
-                            inner = FMA(K.ksig * S, -thc, inner);            // eq. (reaction-term-SigmaP1-P) / 2
-                        }
-                        fh = q * inner;
-                    }
-                    dph = W * FMA(K.klap, lap, fh);
-                }
+        }
+        // ---- Allen-Cahn rate (eq. Allen-Cahn-equation): dphi = W (klap lap + f/2), W = 2 I_W/(alpha xi^2)
+        T dph = T(0);
+        if constexpr (!TEMP) {
+            T W = T(0);
+            if (inside && !bulk) {  // bulk cells: dphi = 0 without arithmetic
+                if constexpr (STATIC) W = sW;
+                else W = FMA(K.wb, Gc, K.wa);
             }
+            const bool need = positive(W);
+            if constexpr (COMPACT) {
+                // Binary64: the cells of the block that need the Allen-Cahn arithmetic are packed into
+                // consecutive slots (warp ballots and a prefix over the block's warps), so each warp runs
+                // it on full lanes; a row of 32 cells mixing glass, bulk and interface cells would run it
+                // on all lanes.  Owners leave their z neighbours, theta and W in the slot; the lateral
+                // neighbours are read from the plane in shared memory.
+                const unsigned m = __ballot_sync(0xffffffffu, need);
+                if (tx == 0) s_wcnt[ty] = __popc(m);
+                __syncthreads();
+                int base = 0, total = 0;
+#pragma unroll
+                for (int w = 0; w < BY; ++w) {
+                    const int c = s_wcnt[w];
+                    base += (w < ty) ? c : 0;
+                    total += c;
+                }
+                const int slot = base + __popc(m & ((1u << tx) - 1u));
+                if (need) {
+                    s_slot_xy[slot] = tx | (ty << 8);
+                    s_slot[0][slot] = phm;
+                    s_slot[1][slot] = php;
+                    s_slot[2][slot] = thc;
+                    s_slot[3][slot] = W;
+                }
+                __syncthreads();
+                for (int q = tid; q < total; q += TX * BY) {
+                    const int xy = s_slot_xy[q];
+                    const int qx = xy & 255, qy = xy >> 8;
+                    // the rate goes back into the slot's first entry (read above by this thread only)
+                    s_slot[0][q] = ac_rate(s_ph[b][qy + 1][qx + 1], s_ph[b][qy + 1][qx], s_ph[b][qy + 1][qx + 2],
+                                           s_ph[b][qy][qx + 1], s_ph[b][qy + 2][qx + 1], s_slot[0][q], s_slot[1][q],
+                                           s_slot[2][q], s_slot[3][q]);
+                }
+                __syncthreads();
+                if (need) dph = s_slot[0][slot];
+            } else if (need) {
+                if constexpr (F32) {
+                    p_xm = s_ph[b][ty + 1][tx]; p_xp = s_ph[b][ty + 1][tx + 2];
+                    p_ym = s_ph[b][ty][tx + 1]; p_yp = s_ph[b][ty + 2][tx + 1];
+                }
+                dph = ac_rate(phc, p_xm, p_xp, p_ym, p_yp, phm, php, thc, W);
+            }
+        }
+        if (inside) {
             // ---- latent-heat coupling
             T dth = T(0);
             if constexpr (STATIC) {
