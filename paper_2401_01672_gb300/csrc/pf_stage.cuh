@@ -179,6 +179,102 @@ __device__ __forceinline__ unsigned long long abs_bits(T v) {
     }
 }
 
+// Allen-Cahn rate of one cell from phi, its six neighbours, theta and W = 2 I_W / (alpha xi^2) > 0
+// (eqs. Allen-Cahn-equation, reaction-term-GradP, reaction-term-SigmaP1-P, Sigma-limiter)
+template <int RX, typename T>
+__device__ __forceinline__ T allen_cahn_rate(const CoefT<T>& K, T pc, T pxm, T pxp, T pym, T pyp, T pzm, T pzp, T th,
+                                             T W) {
+    const T lsum = ((pxm + pxp) + (pym + pyp)) + (pzm + pzp);
+    const T lap = FMA(T(-6), pc, lsum);
+    const T om = T(1) - pc;
+    const T q = pc * om;
+    T inner = pc - T(0.5);
+    T fh;
+    if constexpr (RX == R_GRADP) {
+        const T gx = pxp - pxm, gy = pyp - pym, gz = pzp - pzm;
+        const T gn = dsqrt(FMA(gx, gx, FMA(gy, gy, gz * gz)));
+        fh = FMA(q, inner, K.kgrad * gn * (-th));          // eq. (reaction-term-GradP) / 2
+    } else {
+        if (!le_nonneg(pc, K.eps0) && !le_nonneg(om, K.eps0)) {
+            const T S = sigma_lim(pc, K) * sigma_lim(om, K);
+            inner = FMA(K.ksig * S, -th, inner);            // eq. (reaction-term-SigmaP1-P) / 2
+        }
+        fh = q * inner;
+    }
+    return W * FMA(K.klap, lap, fh);
+}
+
+// End of a tile: stage 5 folds the block's largest |2k1 - 9k3 + 8k4 - k5| into the error maximum (one
+// atomicMax on the binary64 bit pattern, scaled by dt/30); stage 1 adds the block's pore-bulk counts and
+// folds its largest |dphi/dt| (warp shuffles, then shared memory across the block's warps).
+template <int STAGE, bool HAS_PH, bool F32, int BY>
+__device__ __forceinline__ void publish_block(Ctrl* ctrl, unsigned long long ebits, unsigned int icount,
+                                              unsigned int pcount, unsigned long long rbits) {
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    if constexpr (STAGE == 5) {
+        // block max of |E| -> one atomicMax on the binary64 bit pattern (valid for E >= 0; NaN/Inf
+        // patterns sort above every finite value)
+        unsigned long long e = ebits;
+        if constexpr (F32) {
+            const unsigned fb = (unsigned)e;
+            e = (fb >= 0x7F800000u) ? 0x7FF0000000000000ULL
+                                    : (unsigned long long)__double_as_longlong((double)__uint_as_float(fb));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, e, o);
+            e = v > e ? v : e;
+        }
+        __shared__ unsigned long long s_red[BY];
+        if (tx == 0) s_red[ty] = e;
+        __syncthreads();
+        if (ty == 0) {
+            unsigned long long v = tx < BY ? s_red[tx] : 0ULL;
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+                v = w > v ? w : v;
+            }
+            if (tx == 0 && v > 0ULL) {
+                if (v < 0x7FF0000000000000ULL)  // finite: scale by dt/30 (binary64)
+                    v = (unsigned long long)__double_as_longlong(__longlong_as_double((long long)v) * ctrl->sc[7]);
+                atomicMax(&ctrl->err_bits, v);
+            }
+        }
+    }
+    if constexpr (STAGE == 1 && HAS_PH) {
+        // block sums of the two counts -> one atomicAdd each; block max of |dphi/dt| -> one atomicMax
+        unsigned int ci = icount, cp = pcount;
+        unsigned long long r = rbits;
+        if constexpr (F32) {
+            const unsigned fb = (unsigned)r;
+            r = (fb >= 0x7F800000u) ? 0x7FF0000000000000ULL
+                                    : (unsigned long long)__double_as_longlong((double)__uint_as_float(fb));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            ci += __shfl_xor_sync(0xffffffffu, ci, o);
+            cp += __shfl_xor_sync(0xffffffffu, cp, o);
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, r, o);
+            r = v > r ? v : r;
+        }
+        __shared__ unsigned int s_cnt[2][BY];
+        __shared__ unsigned long long s_rate[BY];
+        if (tx == 0) { s_cnt[0][ty] = ci; s_cnt[1][ty] = cp; s_rate[ty] = r; }
+        __syncthreads();
+        if (ty == 0) {
+            unsigned int v = tx < BY ? s_cnt[0][tx] : 0u, w = tx < BY ? s_cnt[1][tx] : 0u;
+            unsigned long long m = tx < BY ? s_rate[tx] : 0ULL;
+            for (int o = 16; o > 0; o >>= 1) {
+                v += __shfl_xor_sync(0xffffffffu, v, o);
+                w += __shfl_xor_sync(0xffffffffu, w, o);
+                const unsigned long long x = __shfl_xor_sync(0xffffffffu, m, o);
+                m = x > m ? x : m;
+            }
+            if (tx == 0 && v > 0u) atomicAdd(&ctrl->ice_count, (unsigned long long)v);
+            if (tx == 0 && w > 0u) atomicAdd(&ctrl->pore_count, (unsigned long long)w);
+            if (tx == 0 && m > 0ULL) atomicMax(&ctrl->rate_bits, m);
+        }
+    }
+}
+
 // One tile (32 x BY columns, one z chunk) of one stage.  (bxi, byi, bzi) is the tile's position in
 // the grid's tile lattice.  Called by the single-grid kernel (one block per tile) and by the batched
 // persistent kernel (blocks loop over the tiles of all active instances).
@@ -318,27 +414,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
         s_ph[b][y][x] = ph;
     };
 
-    // Allen-Cahn rate of one cell from phi, its six neighbours, theta and W = 2 I_W / (alpha xi^2) > 0
-    // (eqs. Allen-Cahn-equation, reaction-term-GradP, reaction-term-SigmaP1-P, Sigma-limiter)
     auto ac_rate = [&](T pc, T pxm, T pxp, T pym, T pyp, T pzm, T pzp, T th, T W) -> T {
-        const T lsum = ((pxm + pxp) + (pym + pyp)) + (pzm + pzp);
-        const T lap = FMA(T(-6), pc, lsum);
-        const T om = T(1) - pc;
-        const T q = pc * om;
-        T inner = pc - T(0.5);
-        T fh;
-        if constexpr (RX == R_GRADP) {
-            const T gx = pxp - pxm, gy = pyp - pym, gz = pzp - pzm;
-            const T gn = dsqrt(FMA(gx, gx, FMA(gy, gy, gz * gz)));
-            fh = FMA(q, inner, K.kgrad * gn * (-th));          // eq. (reaction-term-GradP) / 2
-        } else {
-            if (!le_nonneg(pc, K.eps0) && !le_nonneg(om, K.eps0)) {
-                const T S = sigma_lim(pc, K) * sigma_lim(om, K);
-                inner = FMA(K.ksig * S, -th, inner);            // eq. (reaction-term-SigmaP1-P) / 2
-            }
-            fh = q * inner;
-        }
-        return W * FMA(K.klap, lap, fh);
+        return allen_cahn_rate<RX>(K, pc, pxm, pxp, pym, pyp, pzm, pzp, th, W);
     };
     // binary64 (full and micro models): the Allen-Cahn arithmetic runs on compacted slots (not for the
     // 16-row blocks, whose planes already fill most of the 48 KiB of static shared memory)
@@ -672,68 +749,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
         __syncthreads();
     }
 
-    if constexpr (STAGE == 5) {
-        // block max of |E| -> one atomicMax on the binary64 bit pattern (valid for E >= 0; NaN/Inf
-        // patterns sort above every finite value)
-        unsigned long long e = ebits;
-        if constexpr (F32) {
-            const unsigned fb = (unsigned)e;
-            e = (fb >= 0x7F800000u) ? 0x7FF0000000000000ULL
-                                    : (unsigned long long)__double_as_longlong((double)__uint_as_float(fb));
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long v = __shfl_xor_sync(0xffffffffu, e, o);
-            e = v > e ? v : e;
-        }
-        __shared__ unsigned long long s_red[BY];
-        if (tx == 0) s_red[ty] = e;
-        __syncthreads();
-        if (ty == 0) {
-            unsigned long long v = tx < BY ? s_red[tx] : 0ULL;
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
-                v = w > v ? w : v;
-            }
-            if (tx == 0 && v > 0ULL) {
-                if (v < 0x7FF0000000000000ULL)  // finite: scale by dt/30 (binary64)
-                    v = (unsigned long long)__double_as_longlong(__longlong_as_double((long long)v) * ctrl->sc[7]);
-                atomicMax(&ctrl->err_bits, v);
-            }
-        }
-    }
-    if constexpr (STAGE == 1 && HAS_PH) {
-        // block sums of the two counts -> one atomicAdd each; block max of |dphi/dt| -> one atomicMax
-        unsigned int ci = icount, cp = pcount;
-        unsigned long long r = rbits;
-        if constexpr (F32) {
-            const unsigned fb = (unsigned)r;
-            r = (fb >= 0x7F800000u) ? 0x7FF0000000000000ULL
-                                    : (unsigned long long)__double_as_longlong((double)__uint_as_float(fb));
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            ci += __shfl_xor_sync(0xffffffffu, ci, o);
-            cp += __shfl_xor_sync(0xffffffffu, cp, o);
-            const unsigned long long v = __shfl_xor_sync(0xffffffffu, r, o);
-            r = v > r ? v : r;
-        }
-        __shared__ unsigned int s_cnt[2][BY];
-        __shared__ unsigned long long s_rate[BY];
-        if (tx == 0) { s_cnt[0][ty] = ci; s_cnt[1][ty] = cp; s_rate[ty] = r; }
-        __syncthreads();
-        if (ty == 0) {
-            unsigned int v = tx < BY ? s_cnt[0][tx] : 0u, w = tx < BY ? s_cnt[1][tx] : 0u;
-            unsigned long long m = tx < BY ? s_rate[tx] : 0ULL;
-            for (int o = 16; o > 0; o >>= 1) {
-                v += __shfl_xor_sync(0xffffffffu, v, o);
-                w += __shfl_xor_sync(0xffffffffu, w, o);
-                const unsigned long long x = __shfl_xor_sync(0xffffffffu, m, o);
-                m = x > m ? x : m;
-            }
-            if (tx == 0 && v > 0u) atomicAdd(&ctrl->ice_count, (unsigned long long)v);
-            if (tx == 0 && w > 0u) atomicAdd(&ctrl->pore_count, (unsigned long long)w);
-            if (tx == 0 && m > 0ULL) atomicMax(&ctrl->rate_bits, m);
-        }
-    }
+    publish_block<STAGE, HAS_PH, F32, BY>(ctrl, ebits, icount, pcount, rbits);
     __syncthreads();  // the block may start another tile: shared memory is reused
     (void)tgm;
 }

@@ -32,16 +32,23 @@ def rel(a, b):
     return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300))
 
 
-@pytest.mark.parametrize("model,rx", [(I.MODEL_FULL, I.REACT_SIGMAP1P), (I.MODEL_FULL, I.REACT_GRADP),
-                                      (I.MODEL_TEMP, I.REACT_SIGMAP1P), (I.MODEL_MICRO, I.REACT_SIGMAP1P)])
-def test_fp32_rhs_against_oracle(env, model, rx):
+# ragged tiles in x, y and z; more than one tile along x
+FP32_SHAPES = [(45, 38, 29), (46, 38, 29), (130, 9, 20)]
+ALL_FACES = I.FACE_XM | I.FACE_XP | I.FACE_YM | I.FACE_YP | I.FACE_ZM | I.FACE_ZP
+
+
+@pytest.mark.parametrize("shape", FP32_SHAPES)
+@pytest.mark.parametrize("model,rx,harmonic,faces",
+                         [(I.MODEL_FULL, I.REACT_SIGMAP1P, 0, I.FACE_ZP), (I.MODEL_FULL, I.REACT_GRADP, 0, I.FACE_ZP),
+                          (I.MODEL_TEMP, I.REACT_SIGMAP1P, 0, I.FACE_ZP), (I.MODEL_MICRO, I.REACT_SIGMAP1P, 0, 0),
+                          (I.MODEL_FULL, I.REACT_SIGMAP1P, 1, ALL_FACES)])
+def test_fp32_rhs_against_oracle(env, model, rx, harmonic, faces, shape):
     """Right-hand side in binary32 on binary32 inputs: relative to the field maximum the error stays
     at the level of binary32 rounding of the inputs amplified by the stencil's cancellation."""
     torch, pf, oracle = env
-    shape = (45, 38, 29)
     h = 2e-4 if model != I.MODEL_MICRO else 1e-6
     p = I.default_params(xi=1.3 * h, xi_G=0.4 * h, alpha=4.17e6 if model != I.MODEL_MICRO else 3e9,
-                         dirichlet_faces=I.FACE_ZP, theta_freeze=-5.0, theta_micro=-0.7)
+                         dirichlet_faces=faces, theta_freeze=-5.0, theta_micro=-0.7, harmonic_mean=harmonic)
     th, ph, G = I.random_fields(shape, 77 + model, theta_scale=3.0)
     # the binary32 form sees binary32-rounded inputs; the oracle gets the same rounded values
     th32, ph32, G32 = (v.astype(np.float32) for v in (th, ph, G))
@@ -166,6 +173,29 @@ def test_lognormal_crop_freeze_thaw_both_forms(env, lognormal_crop):
                 assert duwc <= 5e-3
         g.close()
     print("\n" + "\n".join(report))
+
+
+@pytest.mark.parametrize("shape", [(45, 30, 21), (46, 30, 21), (130, 9, 20)])
+def test_fp32_forced_steps_against_oracle(env, shape):
+    """Five forced Merson steps of the binary32-field form (all five stage kernels) against the binary64
+    oracle at every cell, full model with Dirichlet faces on all sides, ragged tiles."""
+    torch, pf, oracle = env
+    h = 3e-4
+    p = I.default_params(xi=h, xi_G=0.4 * h, alpha=4.17e6, dirichlet_faces=ALL_FACES, theta_freeze=-5.0)
+    th, ph, G = I.random_fields(shape, 404, theta_scale=2.0, smooth=1)
+    dt = 0.01
+    g = pf.Grid(shape, h, I.MODEL_FULL, I.REACT_SIGMAP1P, I.PREC_FP32, p)
+    g.set_glass(G)
+    g.set_state(th, ph, 0.0, dt)
+    g.set_tiles(4, 7)
+    s = g.run_fixed(5, dt)
+    assert s["n_accepted"] == 5
+    gth, gph, _, _ = g.get_state()
+    g.close()
+    o = oracle.Oracle(shape, h, "full", "sigmap1p", p)
+    r = o.run(G, th, ph, 0.0, dt, 5 * dt, 1.0, 5, fixed=True)
+    assert float(np.max(np.abs(gth - r["theta"]))) <= 1e-4
+    assert float(np.max(np.abs(gph - r["phi"]))) <= 1e-4
 
 
 @pytest.mark.slow

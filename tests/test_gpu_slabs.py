@@ -24,7 +24,7 @@ def env():
 def bead_case(n3=44):
     """A full-model bead crop, cold top face switching to warm at t_freeze (so the run crosses the
     Dirichlet switch), ice seed on the top planes."""
-    shape = (37, 30, n3)
+    shape = (38, 30, n3)
     h = 3e-4
     sv, _ = I.packing_boolean(shape, 0.55, I.uniform_radius(5.0, 8.0), 31)
     p = I.default_params(xi=h, xi_G=0.4 * h, alpha=I.ALPHA_MACRO["large"], zeta=2.0, dirichlet_faces=I.FACE_ZP,
