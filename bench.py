@@ -53,13 +53,14 @@ BYTES_F32 = [36, 28, 44, 44, 68]            # sum 220 = 44 B per cell-stage
 # (blends 6+6+6, fluxes 24, Allen-Cahn 16, latent coupling 6) plus each stage's combination.
 FLOPS_RHS = 64
 FLOPS_COMB = [4, 6, 8, 12, 24]
-# DRAM traffic per cell of the binary64 stage-5 kernel from one ncu capture at 192^3
-# (dram__bytes_read.sum + dram__bytes_write.sum = 1144.4 MB over 7,077,888 cells).  None once the
-# kernel changes until it is captured again.  The kernel itself is written to move 160 B/cell: the
-# method's 104 B plus 56 B of precomputed per-cell blend coefficients, read instead of recomputed on
-# the binary64 pipe that bounds it.
-TRAFFIC_F64_S5_PER_CELL = 161.7
-KERNEL_BYTES_F64_S5 = 160
+# DRAM traffic per cell of the stage-5 kernels from one ncu capture each at 192^3, mid-front state
+# (dram__bytes_read.sum + dram__bytes_write.sum over 7,077,888 cells; None once a kernel changes until
+# it is captured again).  Binary64: 1019.3 MB -- the method's 104 B plus the per-cell blend
+# coefficients (64 B where the Allen-Cahn arithmetic runs, 24 B in the bulk), read instead of
+# recomputed on the binary64 pipe that bounds it.  Binary32 form: 469.3 MB.
+TRAFFIC_F64_S5_PER_CELL = 144.0
+TRAFFIC_F32_S5_PER_CELL = 66.3
+KERNEL_BYTES_F64_S5 = None
 
 
 def shard(items, rank, world):
@@ -781,7 +782,7 @@ def main():
                 "peak_measured_fp64_tflops": fp64_meas, "frac_of_measured": achieved_tf / fp64_meas,
                 "measured_fp32_tflops": fp32_meas, "measured_copy_gbs": copy_meas,
                 "algorithmic_per_launch": {"flops": flops, "bytes": BYTES_F64[top] * w.n_cells},
-                "kernel_bytes_per_launch": (KERNEL_BYTES_F64_S5 * w.n_cells if top == 4 else None),
+                "kernel_bytes_per_launch": (KERNEL_BYTES_F64_S5 * w.n_cells if (top == 4 and KERNEL_BYTES_F64_S5) else None),
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (binary64 pipe)",
                 "hbm_achieved_gbs": BYTES_F64[top] * w.n_cells / (top_ms * 1e-3) / 1e9,
                 "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peak_kind,
@@ -829,7 +830,8 @@ def main():
                          "frac": gbs32 / peaks["hbm_gbs"],
                          "step_gbs": sum(BYTES_F32) * w.n_cells / (sum(prof32[:5]) * 1e-3) / 1e9,
                          "step_frac": sum(BYTES_F32) * w.n_cells / (sum(prof32[:5]) * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                         "traffic": None, "peak_source": peak_kind,
+                         "traffic": (TRAFFIC_F32_S5_PER_CELL * w.n_cells if (top32 == 4 and TRAFFIC_F32_S5_PER_CELL) else None),
+                         "peak_source": peak_kind,
                          "stage_ms": dict(zip(stage_names, prof32))}}
         g32.close()
 
