@@ -11,8 +11,8 @@
  *     same layout.
  *   - Convolutions: 3x3x3 taps, zero padding 1, stride 1.  Weights [27][Cout][Cin] bfloat16, tap
  *     t = (dz+1)*9 + (dy+1)*3 + (dx+1).  Forward and backward-data products on the fifth-generation
- *     tensor cores (TMA-staged operands, tcgen05.mma with fp32 accumulators in tensor memory);
- *     weight gradients with mma.sync m16n8k16 (bf16 in, fp32 accumulation).
+ *     tensor cores (TMA-staged operands, tcgen05.mma with fp32 accumulators in tensor memory), weight
+ *     gradients too (over a packed copy of the operands).
  *   - All pointers are DEVICE pointers borrowed for the call (caller-owned, e.g. torch tensors);
  *     16-byte alignment of every bf16 row is required (ld, off multiples of 8).  Work is enqueued on
  *     `stream` (cudaStream_t, NULL = legacy default stream); nothing synchronises.
@@ -49,9 +49,15 @@ pf_status pfnn_status(int* failed);
  * it.  The setting applies to one call only.  Nothing faults: the withheld stage is an empty wait. */
 pf_status pfnn_test_withhold_stage(int stage, long long tries);
 
-/* Weight gradient: dw[t][co][ci] += sum_v dy[v][co] x[v + off(t)][ci]  (fp32 atomics, split over voxels). */
+/* Weight gradient: dw[t][co][ci] += sum_v dy[v][co] x[v + off(t)][ci], on the fifth-generation tensor cores:
+ * dy and x are packed channel-major over the zero-padded grid (dy three times, shifted by dx = -1, 0, 1) in
+ * the caller-owned device scratch `work` (16-byte aligned, at least pfnn_conv3d_wgrad_work_bytes bytes,
+ * overwritten), then a GEMM over the packed voxels with rows (tap, co) -- 128 / cout taps per MMA tile --
+ * and columns ci accumulates in TMEM; each CTA adds its voxel chunk's partial sums into dw with FP32
+ * atomics.  cout in {16, 32, 64, 128}, cin a multiple of 16 up to 256. */
+long long pfnn_conv3d_wgrad_work_bytes(int cout, int cin, int n, int d, int h, int wd);
 pf_status pfnn_conv3d_wgrad(const void* dy, int lddy, int dyoff, int cout, const void* x, int ldx, int xoff, int cin,
-                            float* dw, int n, int d, int h, int wd, void* stream);
+                            float* dw, int n, int d, int h, int wd, void* work, long long work_bytes, void* stream);
 
 /* db[c] += sum_v dz[v][off + c]  (dz fp32 with ld channels per voxel). */
 pf_status pfnn_bias_grad(const float* dz, int ld, int off, int c, long long nvox, float* db, void* stream);

@@ -1,7 +1,7 @@
 // Kernels of the learned warm start: a 3D convolutional encoder-decoder trained and run with BF16
 // activations and weights, FP32 accumulation, FP32 master weights and gradients.  The forward and
-// backward-data convolutions run on tcgen05 (pfnn_umma.cu); this file holds the weight gradient
-// (mma.sync m16n8k16) and the data-movement, head and optimiser kernels.
+// backward-data convolutions and the weight gradient run on tcgen05 (pfnn_umma.cu); this file holds the
+// data-movement, head and optimiser kernels.
 //
 // Layout: activations N x D x H x W x C (channels last), bf16; a tensor may be a channel slice
 // [off, off + C) of a wider buffer with ld channels per voxel (skip concatenation is free).
@@ -11,8 +11,7 @@
 // Implicit GEMM (forward): D[v][co] = sum over (t, ci) of X[v + off(t)][ci] W[t][co][ci].
 // Backward data is the same GEMM on dY with flipped taps and transposed weights [27][Cin][Cout]:
 //   dX[v][ci] = sum over (t, co) of dY[v - off(t)][co] W[t][co][ci].
-// Backward weight, per tap: dW[t][co][ci] = sum over v of dY[v][co] X[v + off(t)][ci] (split over
-// voxel chunks, FP32 atomics).
+// Backward weight, per tap: dW[t][co][ci] = sum over v of dY[v][co] X[v + off(t)][ci] (pfnn_umma.cu).
 #include "../../include/pfnn.h"
 #include "pf_internal.cuh"
 
@@ -20,19 +19,6 @@
 #include <cstdint>
 
 namespace {
-
-constexpr int BM = 64;     // voxels (rows) per block tile
-constexpr int KC = 16;     // k chunk = one mma k step
-constexpr int KP = 24;     // padded smem row length (bf16): conflict-free fragment loads
-constexpr int NTHR = 128;  // 4 warps, 16 rows each
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
 
 // voxel index -> coordinates
 __device__ __forceinline__ void vox_coord(long long v, int D, int H, int W, int& b, int& z, int& y, int& x) {
@@ -44,85 +30,6 @@ __device__ __forceinline__ void vox_coord(long long v, int D, int H, int W, int&
     b = (int)(r / D);
 }
 
-// Weight gradient for one tap per blockIdx.y: dW[t][co][ci] += sum over the block's voxel chunk of
-// dY[v][co] X[v + off(t)][ci].  M = co (rows, BM = 64 with masking), N = ci (BNW columns), k = voxels.
-constexpr int VCHUNK = 1024;
-template <int BNW>
-__global__ void __launch_bounds__(NTHR)
-k_conv_wgrad(const __nv_bfloat16* __restrict__ dy, int lddy, int dyoff, int cout, const __nv_bfloat16* __restrict__ x,
-             int ldx, int xoff, int cin, float* __restrict__ dw, int D, int H, int W, long long nvox) {
-    __shared__ __align__(16) __nv_bfloat16 As[BM][KP];   // [co][v]
-    __shared__ __align__(16) __nv_bfloat16 Bs[BNW][KP];  // [ci][v]
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = lane >> 2, t4 = lane & 3;
-    const int tap = blockIdx.y;
-    const int dz = tap / 9 - 1, dyy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-    const int co0 = blockIdx.z * BM;
-    const int ci0 = (int)(blockIdx.x % ((cin + BNW - 1) / BNW)) * BNW;
-    const long long vbeg = (long long)(blockIdx.x / ((cin + BNW - 1) / BNW)) * VCHUNK;
-    float acc[BNW / 8][4];
-#pragma unroll
-    for (int j = 0; j < BNW / 8; ++j)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
-
-    for (long long vk = vbeg; vk < vbeg + VCHUNK && vk < nvox; vk += KC) {
-        // A: 16 voxels x 64 co  -> As[co][v]; thread loads 8 co of one voxel
-        for (int r = tid; r < KC * (BM / 8); r += NTHR) {
-            const int vv = r / (BM / 8), cg = (r % (BM / 8)) * 8;
-            const long long v = vk + vv;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (v < nvox && co0 + cg < cout) val = *reinterpret_cast<const uint4*>(dy + v * lddy + dyoff + co0 + cg);
-            const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&val);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) As[cg + q][vv] = e[q];
-        }
-        // B: 16 voxels x BNW ci (shifted input) -> Bs[ci][v]
-        for (int r = tid; r < KC * (BNW / 8); r += NTHR) {
-            const int vv = r / (BNW / 8), cg = (r % (BNW / 8)) * 8;
-            const long long v = vk + vv;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (v < nvox && ci0 + cg < cin) {
-                int b, z, yy, xx;
-                vox_coord(v, D, H, W, b, z, yy, xx);
-                const int sz = z + dz, sy = yy + dyy, sx = xx + dx;
-                if (sz >= 0 && sz < D && sy >= 0 && sy < H && sx >= 0 && sx < W) {
-                    const long long sv = (((long long)b * D + sz) * H + sy) * W + sx;
-                    val = *reinterpret_cast<const uint4*>(x + sv * ldx + xoff + ci0 + cg);
-                }
-            }
-            const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&val);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) Bs[cg + q][vv] = e[q];
-        }
-        __syncthreads();
-        uint32_t a[4];
-        const int r0 = warp * 16 + g;
-        a[0] = *reinterpret_cast<const uint32_t*>(&As[r0][2 * t4]);
-        a[1] = *reinterpret_cast<const uint32_t*>(&As[r0 + 8][2 * t4]);
-        a[2] = *reinterpret_cast<const uint32_t*>(&As[r0][2 * t4 + 8]);
-        a[3] = *reinterpret_cast<const uint32_t*>(&As[r0 + 8][2 * t4 + 8]);
-#pragma unroll
-        for (int j = 0; j < BNW / 8; ++j) {
-            uint32_t b[2];
-            b[0] = *reinterpret_cast<const uint32_t*>(&Bs[j * 8 + g][2 * t4]);
-            b[1] = *reinterpret_cast<const uint32_t*>(&Bs[j * 8 + g][2 * t4 + 8]);
-            mma_bf16(acc[j], a, b);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int j = 0; j < BNW / 8; ++j)
-#pragma unroll
-        for (int hrow = 0; hrow < 2; ++hrow) {
-            const int co = co0 + warp * 16 + g + hrow * 8;
-            const int ci = ci0 + j * 8 + 2 * t4;
-            if (co >= cout || ci >= cin) continue;
-            float* p = dw + ((long long)tap * cout + co) * cin + ci;
-            atomicAdd(p, acc[j][hrow * 2]);
-            atomicAdd(p + 1, acc[j][hrow * 2 + 1]);
-        }
-}
 
 __global__ void k_bias_grad(const float* __restrict__ dz, int ld, int off, int c, long long nvox, float* db) {
     // one block per channel group of 32 channels x 8 voxel lanes
@@ -324,28 +231,6 @@ using bf16 = __nv_bfloat16;
 
 extern "C" {
 
-pf_status pfnn_conv3d_wgrad(const void* dy, int lddy, int dyoff, int cout, const void* x, int ldx, int xoff, int cin,
-                            float* dw, int n, int d, int h, int wd, void* stream) {
-    if (!dy || !x || !dw || cin < 16 || cin % 16 || cout % 8 || !aligned8(lddy) || !aligned8(dyoff) ||
-        !aligned8(ldx) || !aligned8(xoff))
-        return PF_E_INVALID;
-    const long long nvox = (long long)n * d * h * wd;
-    const int bnw = cin >= 64 ? 64 : (cin > 16 ? 32 : 16);
-    const int nci = (cin + bnw - 1) / bnw;
-    dim3 grid((unsigned)(((nvox + VCHUNK - 1) / VCHUNK) * nci), 27, (unsigned)((cout + BM - 1) / BM));
-    cudaStream_t s = (cudaStream_t)stream;
-    if (bnw == 64)
-        k_conv_wgrad<64><<<grid, NTHR, 0, s>>>((const bf16*)dy, lddy, dyoff, cout, (const bf16*)x, ldx, xoff, cin, dw, d,
-                                               h, wd, nvox);
-    else if (bnw == 32)
-        k_conv_wgrad<32><<<grid, NTHR, 0, s>>>((const bf16*)dy, lddy, dyoff, cout, (const bf16*)x, ldx, xoff, cin, dw, d,
-                                               h, wd, nvox);
-    else
-        k_conv_wgrad<16><<<grid, NTHR, 0, s>>>((const bf16*)dy, lddy, dyoff, cout, (const bf16*)x, ldx, xoff, cin, dw, d,
-                                               h, wd, nvox);
-    pfgb::count_launch();
-    return cudaGetLastError() == cudaSuccess ? PF_OK : PF_E_CUDA;
-}
 
 pf_status pfnn_bias_grad(const float* dz, int ld, int off, int c, long long nvox, float* db, void* stream) {
     if (!dz || !db || c < 1) return PF_E_INVALID;

@@ -96,6 +96,8 @@ struct pfnn_net {
     float* grad[NBUF] = {};                // fp32 gradients of the activations
     float *dz_f = nullptr, *logit_grad = nullptr, *prob = nullptr;
     void* dz_b = nullptr;
+    void* wg_work = nullptr;               // scratch of the weight gradients
+    long long wg_bytes = 0;
     double* loss = nullptr;
     bool have_target = false;
     std::vector<void*> allocs, act_allocs;
@@ -128,6 +130,8 @@ void free_acts(pfnn_net* net) {
     }
     net->dz_f = net->logit_grad = net->prob = nullptr;
     net->dz_b = nullptr;
+    net->wg_work = nullptr;
+    net->wg_bytes = 0;
     net->n = net->S = 0;
 }
 
@@ -148,7 +152,16 @@ pf_status ensure_acts(pfnn_net* net, int n, int S) {
     net->dz_b = nalloc(net->act_allocs, 2 * nvox * 128);
     net->logit_grad = (float*)nalloc(net->act_allocs, 4 * nvox);
     net->prob = (float*)nalloc(net->act_allocs, 4 * nvox);
-    if (!net->dz_f || !net->dz_b || !net->logit_grad || !net->prob) return nfail(net, PF_E_OOM, "work buffers");
+    long long wg = 0;
+    for (int q = 0; q < NCONV; ++q) {
+        const int sd = S >> kLayers[q].lev;
+        const long long b = pfnn_conv3d_wgrad_work_bytes(kLayers[q].cout, kLayers[q].cin, n, sd, sd, sd);
+        wg = b > wg ? b : wg;
+    }
+    net->wg_work = nalloc(net->act_allocs, (size_t)wg);
+    net->wg_bytes = wg;
+    if (!net->dz_f || !net->dz_b || !net->logit_grad || !net->prob || !net->wg_work)
+        return nfail(net, PF_E_OOM, "work buffers");
     net->n = n;
     net->S = S;
     return PF_OK;
@@ -387,7 +400,7 @@ pf_status pfnn_net_backward(pfnn_net* net) {
                                       net->dz_f, net->dz_b, s), "relu backward");
         NN_CK(net, pfnn_bias_grad(net->dz_f, L.cout, 0, L.cout, nvox, P.gb, s), "bias gradient");
         NN_CK(net, pfnn_conv3d_wgrad(net->dz_b, L.cout, 0, L.cout, net->act[L.src], kBufC[L.src], L.soff, L.cin, P.gw,
-                                     d[0], d[1], d[2], d[3], s), "weight gradient");
+                                     d[0], d[1], d[2], d[3], net->wg_work, net->wg_bytes, s), "weight gradient");
         if (L.src != IN0) {
             NN_CK(net, pfnn_weight_transpose(P.wb, P.wt, L.cout, L.cin, s), "weight transpose");
             NN_CK(net, pfnn_conv3d(net->dz_b, L.cout, 0, P.wt, L.cout, L.cin, nullptr, 0, 1, nullptr, net->grad[L.src],

@@ -296,6 +296,163 @@ k_conv_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
 }
 
+// ---------------------------------------------------------------- weight gradient on tcgen05
+// dW[t][co][ci] = sum over voxels v of dY[v][co] X[v + off(t)][ci] (zero padding) is, with u = v + off(t),
+// sum over u of dY[u - off(t)][co] X[u][ci]: a GEMM whose reduction runs over voxels.  Both tensors are
+// first packed channel-major over a zero-padded grid (rows of W' = W + 2 rounded up to 8 cells, planes of
+// (H + 2) W', samples of (D + 2) planes), so that a tap's offset is a constant shift of the packed voxel
+// index; dY is packed three times, shifted by dx = -1, 0, +1, so that the remaining shift
+// dz (H + 2) W' + dy W' keeps the TMA coordinate a multiple of 8 elements (16 bytes).
+//   A (M = 128 rows): 128 / cout taps x cout output channels; tap j's rows are one TMA box of the dx-copy,
+//                     64 voxels wide, shifted by the tap's offset (out-of-range voxels filled with zeros);
+//   B (N = cin):      one TMA box of the packed X, 64 voxels wide;
+//   K:                the packed voxels of the CTA's chunk, 64 per pipeline stage (4 MMAs of K = 16).
+// Both operands are K-major with 128-byte rows (the 128-byte swizzle), as in k_conv_umma.  Each CTA adds
+// its chunk's partial products into dW with FP32 atomics (split over voxel chunks).
+struct WgArgs {
+    int cout, cin, taps_per_tile;
+    int kb_per_cta;               // k blocks (of 64 packed voxels) per CTA
+    long long nkb;                // k blocks in total
+    int plane_p, row_p;           // packed plane and row lengths
+    int stages;
+    unsigned a_bytes, stage_bytes;
+    unsigned idesc;
+    unsigned long long desc_hi;
+    int tmem_cols;
+    long long tries;
+    float* dw;
+};
+
+__global__ void __launch_bounds__(UTHR)
+k_wgrad_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const WgArgs p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    const int S = p.stages;
+    unsigned char* ctl = sm + (size_t)S * p.stage_bytes;
+    const uint32_t full0 = smem_u32(ctl);
+    const uint32_t empty0 = full0 + 8u * S;
+    const uint32_t accum = empty0 + 8u * S;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ctl + 16 * S + 8);
+    __shared__ int s_fail;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t0 = blockIdx.x * p.taps_per_tile;
+    const int ntap = min(p.taps_per_tile, 27 - t0);
+    const long long kb0 = (long long)blockIdx.y * p.kb_per_cta;
+    const int KB = (int)min((long long)p.kb_per_cta, p.nkb - kb0);
+    const unsigned tx_bytes = (unsigned)(ntap * p.cout * 128 + p.cin * 128);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full0 + 8u * s, 1);
+            mbar_init(empty0 + 8u * s, 1);
+        }
+        mbar_init(accum, 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(p.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t sm0 = smem_u32(sm);
+
+    int issued = 0;
+    if (threadIdx.x == 0) {
+        // ---- producer: one stage = the ntap shifted dY boxes and the X box of 64 packed voxels
+        for (int kb = 0; kb < KB; ++kb, ++issued) {
+            const int s = kb % S;
+            const uint32_t use = (uint32_t)(kb / S);
+            if (kb >= S && !mbar_wait(empty0 + 8u * s, (use & 1u) ^ 1u, p.tries)) break;
+            const uint32_t fb = full0 + 8u * s;
+            mbar_expect_tx(fb, tx_bytes);
+            const int k0 = (int)((kb0 + kb) * 64);
+            const uint32_t a_dst = sm0 + (uint32_t)s * p.stage_bytes;
+            for (int j = 0; j < ntap; ++j) {
+                const int t = t0 + j;
+                const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+                tma_load_2d(a_dst + (uint32_t)(j * p.cout * 128), &tmA, fb, k0 - (dz * p.plane_p + dy * p.row_p),
+                            (dx + 1) * p.cout);
+            }
+            tma_load_2d(a_dst + p.a_bytes, &tmB, fb, k0, 0);
+        }
+    } else if (threadIdx.x == 32) {
+        // ---- MMA issuer: 4 MMAs (K = 16 packed voxels each) per stage into the TMEM accumulator
+        bool ok = true;
+        for (int kb = 0; kb < KB && ok; ++kb) {
+            const int s = kb % S;
+            const uint32_t use = (uint32_t)(kb / S);
+            ok = mbar_wait(full0 + 8u * s, use & 1u, p.tries);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_addr = sm0 + (uint32_t)s * p.stage_bytes;
+            const uint32_t b_addr = a_addr + p.a_bytes;
+            for (int k = 0; k < 4; ++k)
+                umma_f16(tmem, sdesc(a_addr + 32u * k, p.desc_hi), sdesc(b_addr + 32u * k, p.desc_hi), p.idesc,
+                         (kb > 0 || k > 0) ? 1u : 0u);
+            umma_commit(empty0 + 8u * s);
+        }
+        if (!ok) s_fail = 1;
+        umma_commit(accum);
+    }
+    __syncwarp();
+    __syncthreads();
+
+    // ---- epilogue: TMEM lane r = row (tap t0 + r / cout, channel r % cout), columns = input channels
+    const bool ready = mbar_wait(accum, 0u, p.tries) && !s_fail && KB > 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int r = warp * 32 + lane;
+    const int j = r / p.cout, co = r - j * p.cout;
+    const bool live = ready && j < ntap;
+    for (int c0 = 0; c0 < p.cin; c0 += 16) {
+        float o[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, o);  // whole warp, always
+        if (!live) continue;
+        float* dst = p.dw + ((long long)(t0 + j) * p.cout + co) * p.cin + c0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) atomicAdd(dst + q, o[q]);
+    }
+
+    if (threadIdx.x == 0 && !ready) {
+        for (int kb = issued - S < 0 ? 0 : issued - S; kb < issued; ++kb)
+            mbar_wait(full0 + 8u * (kb % S), (uint32_t)(kb / S) & 1u, p.tries);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 2) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
+    }
+}
+
+// Packing for the weight gradient: X and the three dx-shifted copies of dY, channel-major over the padded
+// grid (see k_wgrad_umma); the buffers are zeroed before, so the padding stays zero.
+__global__ void k_wgrad_pack(const __nv_bfloat16* __restrict__ dy, int lddy, int dyoff, int cout,
+                             const __nv_bfloat16* __restrict__ x, int ldx, int xoff, int cin, int D, int H, int W,
+                             int Wp, long long nvox, long long vp64, __nv_bfloat16* __restrict__ A3,
+                             __nv_bfloat16* __restrict__ XB) {
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x) {
+        const int xx = (int)(v % W);
+        long long q = v / W;
+        const int yy = (int)(q % H);
+        q /= H;
+        const int zz = (int)(q % D);
+        const long long b = q / D;
+        const long long vp = ((b * (D + 2) + zz + 1) * (H + 2) + yy + 1) * (long long)Wp + xx + 1;
+        for (int c = 0; c < cout; ++c) {
+            const __nv_bfloat16 val = dy[v * lddy + dyoff + c];
+            for (int d = 0; d < 3; ++d) A3[((long long)d * cout + c) * vp64 + vp + (d - 1)] = val;
+        }
+        for (int c = 0; c < cin; ++c) XB[(long long)c * vp64 + vp] = x[v * ldx + xoff + c];
+    }
+}
+
 // ---------------------------------------------------------------- host side
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -411,6 +568,101 @@ pf_status pfnn_conv3d(const void* x, int ldx, int xoff, const void* w, int cin, 
     const long long blocks = (long long)a.tx * a.ty * a.tz * n;
     if (blocks > 0x7FFFFFFFLL) return PF_E_RANGE;
     k_conv_umma<<<(unsigned)blocks, UTHR, smem, (cudaStream_t)stream>>>(mA, mB, a);
+    pfgb::count_launch();
+    return cudaGetLastError() == cudaSuccess ? PF_OK : PF_E_CUDA;
+}
+
+// packed layout of the weight gradient: padded row W' = W + 2 rounded up to 8, packed voxels rounded to 64
+static void wgrad_layout(int n, int d, int h, int wd, int* wp, long long* vp64) {
+    *wp = (wd + 2 + 7) / 8 * 8;
+    const long long vp = (long long)n * (d + 2) * (h + 2) * (*wp);
+    *vp64 = (vp + 63) / 64 * 64;
+}
+
+long long pfnn_conv3d_wgrad_work_bytes(int cout, int cin, int n, int d, int h, int wd) {
+    if (cout < 1 || cin < 1 || n < 1 || d < 1 || h < 1 || wd < 1) return -1;
+    int wp;
+    long long vp64;
+    wgrad_layout(n, d, h, wd, &wp, &vp64);
+    return 2LL * (3LL * cout + cin) * vp64;
+}
+
+pf_status pfnn_conv3d_wgrad(const void* dy, int lddy, int dyoff, int cout, const void* x, int ldx, int xoff, int cin,
+                            float* dw, int n, int d, int h, int wd, void* work, long long work_bytes, void* stream) {
+    if (!dy || !x || !dw || !work || n < 1 || d < 1 || h < 1 || wd < 1) return PF_E_INVALID;
+    if ((cout != 16 && cout != 32 && cout != 64 && cout != 128) || cin < 16 || cin % 16 || cin > 256 ||
+        lddy < dyoff + cout || ldx < xoff + cin || dyoff < 0 || xoff < 0)
+        return PF_E_INVALID;
+    if (work_bytes < pfnn_conv3d_wgrad_work_bytes(cout, cin, n, d, h, wd) || reinterpret_cast<uintptr_t>(work) % 16)
+        return PF_E_INVALID;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return PF_E_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    int wp;
+    long long vp64;
+    wgrad_layout(n, d, h, wd, &wp, &vp64);
+    bf16* A3 = (bf16*)work;
+    bf16* XB = A3 + 3LL * cout * vp64;
+    if (cudaMemsetAsync(work, 0, (size_t)pfnn_conv3d_wgrad_work_bytes(cout, cin, n, d, h, wd), st) != cudaSuccess)
+        return PF_E_CUDA;
+    const long long nvox = (long long)n * d * h * wd;
+    long long pb = (nvox + 255) / 256;
+    if (pb > 152LL * 32) pb = 152LL * 32;
+    k_wgrad_pack<<<(unsigned)pb, 256, 0, st>>>((const bf16*)dy, lddy, dyoff, cout, (const bf16*)x, ldx, xoff, cin, d, h,
+                                                wd, wp, nvox, vp64, A3, XB);
+    pfgb::count_launch();
+
+    alignas(64) CUtensorMap mA, mB;
+    {
+        const cuuint64_t dims[2] = {(cuuint64_t)vp64, (cuuint64_t)(3 * cout)};
+        const cuuint64_t strides[1] = {(cuuint64_t)vp64 * 2};
+        const cuuint32_t box[2] = {64, (cuuint32_t)cout};
+        const cuuint32_t es[2] = {1, 1};
+        if (enc(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, A3, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return PF_E_INVALID;
+    }
+    {
+        const cuuint64_t dims[2] = {(cuuint64_t)vp64, (cuuint64_t)cin};
+        const cuuint64_t strides[1] = {(cuuint64_t)vp64 * 2};
+        const cuuint32_t box[2] = {64, (cuuint32_t)cin};
+        const cuuint32_t es[2] = {1, 1};
+        if (enc(&mB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, XB, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return PF_E_INVALID;
+    }
+    WgArgs a{};
+    a.cout = cout;
+    a.cin = cin;
+    a.taps_per_tile = UM / cout;
+    const int ntiles = (27 + a.taps_per_tile - 1) / a.taps_per_tile;
+    a.nkb = vp64 / 64;
+    // about four waves of CTAs over the 152 SMs
+    long long chunks = (4LL * 152 + ntiles - 1) / ntiles;
+    if (chunks > a.nkb) chunks = a.nkb;
+    a.kb_per_cta = (int)((a.nkb + chunks - 1) / chunks);
+    chunks = (a.nkb + a.kb_per_cta - 1) / a.kb_per_cta;
+    a.plane_p = (h + 2) * wp;
+    a.row_p = wp;
+    a.a_bytes = (unsigned)(UM * 128);
+    a.stage_bytes = a.a_bytes + round1024((unsigned)(cin * 128));
+    int stages = (int)(98304u / a.stage_bytes);
+    a.stages = stages < 2 ? 2 : (stages > 8 ? 8 : stages);
+    a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(cin >> 3) << 17) | ((unsigned)(UM >> 4) << 24);
+    a.desc_hi = (1ULL << 16) | ((1024ULL >> 4) << 32) | (1ULL << 46) | (umma_layout(64) << 61);
+    a.tmem_cols = cin <= 32 ? 32 : (cin <= 64 ? 64 : (cin <= 128 ? 128 : 256));
+    a.tries = WAIT_TRIES;
+    a.dw = dw;
+    const size_t smem = (size_t)a.stages * a.stage_bytes + 1024 + 16 * a.stages + 16;
+    static std::once_flag wg_once;
+    static cudaError_t wg_err = cudaSuccess;
+    std::call_once(wg_once, [] {
+        wg_err = cudaFuncSetAttribute(k_wgrad_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024 + 2048);
+    });
+    if (wg_err != cudaSuccess) return PF_E_CUDA;
+    k_wgrad_umma<<<dim3((unsigned)ntiles, (unsigned)chunks), UTHR, smem, st>>>(mA, mB, a);
     pfgb::count_launch();
     return cudaGetLastError() == cudaSuccess ? PF_OK : PF_E_CUDA;
 }

@@ -36,7 +36,7 @@ def _lib():
         vp, i, ll, f, d = C.c_void_p, C.c_int, C.c_longlong, C.c_float, C.c_double
         sig = {
             "pfnn_conv3d": [vp, i, i, vp, i, i, vp, i, i, vp, vp, i, i, i, i, i, i, i, vp],
-            "pfnn_conv3d_wgrad": [vp, i, i, i, vp, i, i, i, vp, i, i, i, i, vp],
+            "pfnn_conv3d_wgrad": [vp, i, i, i, vp, i, i, i, vp, i, i, i, i, vp, ll, vp],
             "pfnn_bias_grad": [vp, i, i, i, ll, vp, vp],
             "pfnn_relu_bwd_cast": [vp, i, i, vp, i, i, i, ll, vp, vp, vp],
             "pfnn_weight_transpose": [vp, vp, i, i, vp],
@@ -70,6 +70,8 @@ def _lib():
             fn = getattr(lib, name)
             fn.argtypes = args
             fn.restype = C.c_int
+        lib.pfnn_conv3d_wgrad_work_bytes.argtypes = [i, i, i, i, i, i]
+        lib.pfnn_conv3d_wgrad_work_bytes.restype = ll
         lib.pfnn_net_params.argtypes = []
         lib.pfnn_net_params.restype = C.c_int
         lib.pfnn_net_buffers.argtypes = []

@@ -149,11 +149,43 @@ def test_conv_backward_data_and_weight(env, cin, cout):
     assert L.pfnn_conv3d(nn._p(dyt), cout, 0, nn._p(wtr), cout, cin, None, 0, 1, None, nn._p(dx), cin, 0, 1, n, d, h, w,
                          None) == 0
     dw = torch.zeros((27, cout, cin), dtype=torch.float32, device="cuda")
-    assert L.pfnn_conv3d_wgrad(nn._p(dyt), cout, 0, cout, nn._p(xt), cin, 0, cin, nn._p(dw), n, d, h, w, None) == 0
+    wb = L.pfnn_conv3d_wgrad_work_bytes(cout, cin, n, d, h, w)
+    work = torch.empty(wb, dtype=torch.uint8, device="cuda")
+    assert L.pfnn_conv3d_wgrad(nn._p(dyt), cout, 0, cout, nn._p(xt), cin, 0, cin, nn._p(dw), n, d, h, w, nn._p(work),
+                               wb, None) == 0
     torch.cuda.synchronize()
     assert relerr(dx.cpu().numpy(), O.conv3d_bwd_data(dy, wv).reshape(-1, cin)) <= 2e-5
     assert relerr(dw.cpu().numpy(), O.conv3d_bwd_weight(dy, x)) <= 2e-5
     assert no_failed_waits(nn)
+
+
+@pytest.mark.parametrize("cin,cout,shape", [(16, 16, (1, 5, 3, 9)), (32, 32, (2, 4, 6, 8)), (64, 128, (1, 3, 7, 5)),
+                                            (128, 64, (2, 2, 2, 2)), (16, 128, (1, 9, 4, 17)), (48, 16, (3, 3, 3, 3))])
+def test_conv_weight_gradient_on_tensor_cores(env, cin, cout, shape):
+    """Weight gradient (tcgen05 GEMM over packed, zero-padded voxels, rows = taps x output channels) against
+    the FP64 oracle, element by element: ragged grids, channel slices of wider buffers, accumulation into
+    a non-zero gradient, every tap tile (128 / cout taps per tile, the last one partial)."""
+    torch, nn, O = env
+    L = nn._lib()
+    g = np.random.default_rng(cin * 3 + cout)
+    n, d, h, w = shape
+    xt, x = bf(torch, g.standard_normal((n, d, h, w, cin + 16)))      # input slice [8, 8 + cin)
+    dyt, dy = bf(torch, g.standard_normal((n, d, h, w, cout + 32)))   # gradient slice [16, 16 + cout)
+    base = g.standard_normal((27, cout, cin)).astype(np.float32)
+    dw = torch.from_numpy(base.copy()).cuda()
+    wb = L.pfnn_conv3d_wgrad_work_bytes(cout, cin, n, d, h, w)
+    work = torch.full((wb,), 255, dtype=torch.uint8, device="cuda")   # stale scratch must not matter
+    assert L.pfnn_conv3d_wgrad(nn._p(dyt), cout + 32, 16, cout, nn._p(xt), cin + 16, 8, cin, nn._p(dw), n, d, h, w,
+                               nn._p(work), wb, None) == 0
+    torch.cuda.synchronize()
+    ref = O.conv3d_bwd_weight(dy[..., 16:16 + cout], x[..., 8:8 + cin])
+    assert relerr(dw.cpu().numpy() - base, ref) <= 2e-5
+    assert no_failed_waits(nn)
+    # refused on the host: unsupported channel counts, a short scratch
+    assert L.pfnn_conv3d_wgrad(nn._p(dyt), cout + 32, 16, 48, nn._p(xt), cin + 16, 8, cin, nn._p(dw), n, d, h, w,
+                               nn._p(work), wb, None) == -1
+    assert L.pfnn_conv3d_wgrad(nn._p(dyt), cout + 32, 16, cout, nn._p(xt), cin + 16, 8, cin, nn._p(dw), n, d, h, w,
+                               nn._p(work), wb - 16, None) == -1
 
 
 def test_pool_upsample_head(env):
