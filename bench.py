@@ -47,8 +47,9 @@ TOL = 1e-6
 # Bytes: stencil input fields + glass field + stage-combination operands read, outputs written,
 # each once per cell.  Binary64 path, bytes per cell for stages 1..5:
 BYTES_F64 = [56, 72, 88, 104, 104]          # sum 424 = 84.8 B per cell-stage
-# Binary32-field form (stage buffers and G in 4 B, state y in 8 B):
-BYTES_F32 = [36, 28, 44, 44, 68]            # sum 220 = 44 B per cell-stage
+# Binary32-field form (stage buffers, G and the binary32 copy y32 of the state in 4 B, state y in 8 B;
+# stage 1 reads y and writes y32, k1 and the increment d2; stages 2-5 read y32 and their increment):
+BYTES_F32 = [44, 36, 52, 52, 76]            # sum 260 = 52 B per cell-stage
 # Floating-point operations per cell (FMA = 2, division = 1) of the right-hand side as written
 # (blends 6+6+6, fluxes 24, Allen-Cahn 16, latent coupling 6) plus each stage's combination.
 FLOPS_RHS = 64
@@ -57,9 +58,10 @@ FLOPS_COMB = [4, 6, 8, 12, 24]
 # (dram__bytes_read.sum + dram__bytes_write.sum over 7,077,888 cells; None once a kernel changes until
 # it is captured again).  Binary64: 1019.3 MB -- the method's 104 B plus the per-cell blend
 # coefficients (64 B where the Allen-Cahn arithmetic runs, 24 B in the bulk), read instead of
-# recomputed on the binary64 pipe that bounds it.  Binary32 form: 469.3 MB.
+# recomputed on the binary64 pipe that bounds it.  Binary32 form (increments over a binary32 copy of the
+# state): 531.3 MB, the method's 76 B.
 TRAFFIC_F64_S5_PER_CELL = 144.0
-TRAFFIC_F32_S5_PER_CELL = 66.3
+TRAFFIC_F32_S5_PER_CELL = 75.1
 KERNEL_BYTES_F64_S5 = None
 
 
@@ -295,15 +297,54 @@ def crop_study(pf, w, crop=128, t_freeze=10.0, t_end=20.0):
         g.set_state(c.theta0, c.phi0, 0.0, 0.01)
         rows = []
         for t_stop, ref, ru in zip((t_freeze, t_end), legs, ref_u):
+            t0 = time.perf_counter()
             st = g.run_to(t_stop, TOL, 10 ** 6)
+            el = time.perf_counter() - t0
             th, ph, _, _ = g.get_state()
             u = g.unfrozen_fraction()
-            rows.append({"attempts": [st["n_accepted"], st["n_rejected"]],
+            rows.append({"attempts": [st["n_accepted"], st["n_rejected"]], "wall_s": el,
                          "max_abs_dphi": float(np.max(np.abs(ph - ref["phi"]))),
                          "max_abs_dtheta_K": float(np.max(np.abs(th - ref["theta"]))),
                          "uwc": u["uwc"], "uwc_rel_err": abs(u["uwc"] - ru["uwc"]) / ru["uwc"]})
         g.close()
         out[key] = rows
+    return out
+
+
+def cycle_study(pf, w, stream, tiles, t_freeze=10.0, t_end=20.0):
+    """Time to solution of both precision forms on the whole grid through the freeze-then-thaw cycle
+    (top face -5 K until t_freeze, +2 K until t_end, tolerance 1e-6): attempts and wall time of each leg,
+    the unfrozen water, and the largest phase-field difference between the forms at the end of each leg
+    (the oracle cannot run this size; the crop study compares both forms with it)."""
+    p = dict(w.params)
+    p["t_freeze"] = t_freeze
+    out = {"t_freeze": t_freeze, "t_end": t_end}
+    ph64 = []
+    for prec, key in ((I.PREC_FP64, "f64"), (I.PREC_FP32, "f32_fields")):
+        g = pf.Grid(w.shape, w.h, w.model, w.reaction, prec, p, stream=stream)
+        g.set_geometry(w.spheres, w.x3_cap)
+        g.set_state(w.theta0, w.phi0, 0.0, 0.01)
+        g.set_tiles(*tiles[key])
+        rows = []
+        for leg, t_stop in enumerate((t_freeze, t_end)):
+            t0 = time.perf_counter()
+            st = g.run_to(t_stop, TOL, 10 ** 6)
+            el = time.perf_counter() - t0
+            u = g.unfrozen_fraction()
+            _, ph, _, _ = g.get_state()
+            row = {"attempts": [st["n_accepted"], st["n_rejected"]], "wall_s": el, "uwc": u["uwc"],
+                   "n_ice": u["n_ice"]}
+            if prec == I.PREC_FP64:
+                ph64.append(ph)
+            else:
+                row["max_abs_dphi_vs_f64"] = float(np.max(np.abs(ph - ph64[leg])))
+                row["uwc_rel_vs_f64"] = abs(u["uwc"] - out["f64"][leg]["uwc"]) / out["f64"][leg]["uwc"]
+            rows.append(row)
+            del ph
+        g.close()
+        out[key] = rows
+    out["time_to_solution_ratio"] = (sum(r["wall_s"] for r in out["f64"]) /
+                                     sum(r["wall_s"] for r in out["f32_fields"]))
     return out
 
 
@@ -549,9 +590,12 @@ def run_conv(args, rank, world):
             e1.synchronize()
             ms = e0.elapsed_time(e1) / reps
             tf = 2.0 * 27 * cin * cout * nv / (ms * 1e-3) / 1e12
+            io_gbs = nv * (cin + cout) * 2 / (ms * 1e-3) / 1e9
+            halo = cin in (16, 32) and cout in (16, 32) and side >= 16
             out[label] = {"samples": n, "side": side, "cin": cin, "cout": cout, "ms": ms, "tflops": tf,
                           "frac_of_bf16_peak": tf / peaks["bf16_tflops"],
-                          "io_gbs": nv * (cin + cout) * 2 / (ms * 1e-3) / 1e9}
+                          "kernel": "k_conv_halo" if halo else "k_conv_umma",
+                          "io_gbs": io_gbs, "frac_of_hbm": io_gbs / peaks["hbm_gbs"]}
         nn.check_device()
     top = max(out, key=lambda k: out[k]["tflops"])
     line = {"metric": "warm-start 3x3x3 convolution throughput (forward, tcgen05)", "value": out[top]["tflops"],
@@ -676,6 +720,8 @@ def main():
                          "forms, with the crop error study; sweep48: the 48-instance micro-scale "
                          "sweep, batched binary32 persistent run vs the plain binary64 method")
     ap.add_argument("--no-crop-study", action="store_true", help="full512: skip the 128^3 crop error study")
+    ap.add_argument("--no-cycle", action="store_true",
+                    help="full512: skip the whole-grid freeze-then-thaw cycle of both forms (time to solution)")
     ap.add_argument("--form", default="f64", choices=["f64", "f32"], help="stages: precision form")
     ap.add_argument("--max-steps", type=int, default=600, help="sweep48, uwc: attempt cap per instance")
     ap.add_argument("--macro-n3", type=int, default=100, help="macro: cells along the vessel height (100/200/400)")
@@ -835,9 +881,11 @@ def main():
                          "stage_ms": dict(zip(stage_names, prof32))}}
         g32.close()
 
-    study = None
+    study = cycle = None
     if rank == 0 and args.workload == "full512" and not args.no_crop_study:
         study = crop_study(pf, w)
+    if rank == 0 and args.workload == "full512" and not args.no_cycle and not args.no_fp32_form:
+        cycle = cycle_study(pf, w, stream, {"f64": tiles, "f32_fields": forms["fp32_fields"]["tiles_by_zc"]})
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -861,6 +909,8 @@ def main():
                 "clocks": clk.summary(), "forms": forms, "wall_s_timed": t_wall}
         if study:
             line["crop_error_study"] = study
+        if cycle:
+            line["cycle_time_to_solution"] = cycle
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

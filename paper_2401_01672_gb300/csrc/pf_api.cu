@@ -45,6 +45,7 @@ struct pf_grid {
     void* k1_th = nullptr; void* k1_ph = nullptr;
     void* k3_th = nullptr; void* k3_ph = nullptr;
     void* k4_th = nullptr; void* k4_ph = nullptr;
+    void* y32_th = nullptr; void* y32_ph = nullptr;  // binary32 form of the full model: stage inputs are increments over it
     double* G64 = nullptr;
     float* G32 = nullptr;
     double* statics = nullptr;  // full model, binary64: NSTATIC per-cell coefficient arrays (see StageArgs)
@@ -81,6 +82,8 @@ static pf_status refresh_g32(pf_grid* g);
 static size_t fbytes(const pf_grid* g) { return is_f32(g) ? sizeof(float) : sizeof(double); }
 static bool has_th(const pf_grid* g) { return g->model != PF_MODEL_MICRO; }
 static bool has_ph(const pf_grid* g) { return g->model != PF_MODEL_TEMP; }
+// binary32 form of the full model: stage inputs are increments over a binary32 copy of the state
+static bool has_y32(const pf_grid* g) { return is_f32(g) && g->model == PF_MODEL_FULL; }
 
 static int blocks_for(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
@@ -438,6 +441,7 @@ static StageArgs<T> make_args(pf_grid* g) {
     a.k1_th = (T*)g->k1_th; a.k1_ph = (T*)g->k1_ph;
     a.k3_th = (T*)g->k3_th; a.k3_ph = (T*)g->k3_ph;
     a.k4_th = (T*)g->k4_th; a.k4_ph = (T*)g->k4_ph;
+    a.y32_th = (T*)g->y32_th; a.y32_ph = (T*)g->y32_ph;
     if constexpr (std::is_same<T, float>::value) a.G = g->G32;
     else a.G = g->G64;
     a.zc = g->zc;
@@ -600,6 +604,10 @@ static pf_status create_impl(int n1, int n2, int n3, double h, int model, int re
     if (has_ph(g)) {
         g->y_ph[0] = (double*)AG(8); g->y_ph[1] = (double*)AG(8);
         g->ua_ph = AG(fbytes(g)); g->ub_ph = AG(fbytes(g)); g->k1_ph = A(nf); g->k3_ph = A(nf); g->k4_ph = A(nf);
+    }
+    if (is_f32(g) && model == PF_MODEL_FULL) {
+        g->y32_th = AG(4);
+        g->y32_ph = AG(4);
     }
     g->G64 = (double*)AG(8);
     if (is_f32(g)) g->G32 = (float*)AG(4);
@@ -1522,22 +1530,23 @@ long long pf_batch_iterations(const pf_batch* b) { return b ? b->iters : -1; }
 // error maximum and the pore counts accumulate over all slabs and one controller decides).
 
 namespace {
-// Pointers (local plane 0) of one slab's exchanged buffers: [theta, phi][y0, y1, ua, ub].
+// Pointers (local plane 0) of one slab's exchanged buffers: [theta, phi][y0, y1, ua, ub, y32].
 struct SlabTab {
-    void* f[2][4];
+    void* f[2][5];
     int n3;
     int pad;
 };
 
 // which: 0 = ua, 1 = ub (stage inputs written by the stage just run), 2 = y[cur ^ 1] (the step's
-// candidate state), 3 = y[cur] (the state).  blockIdx.y = cut * 4 + direction * 2 + field.
+// candidate state), 3 = y[cur] (the state), 4 = y32 (the binary32 copy of the state stage 1 writes in
+// the binary32 form of the full model).  blockIdx.y = cut * 4 + direction * 2 + field.
 template <typename TF>
 __global__ void k_halo(const SlabTab* __restrict__ tab, long long plane, int which, int fields,
                        const Ctrl* __restrict__ c) {
     const int r = blockIdx.y;
     const int cut = r >> 2, dir = (r >> 1) & 1, f = r & 1;
     if (!((fields >> f) & 1)) return;
-    const int slot = which < 2 ? 2 + which : (which == 2 ? (c->cur ^ 1) : c->cur);
+    const int slot = which < 2 ? 2 + which : (which == 2 ? (c->cur ^ 1) : (which == 3 ? c->cur : 4));
     const SlabTab& lo = tab[cut];
     const SlabTab& hi = tab[cut + 1];
     const TF* src;
@@ -1582,7 +1591,7 @@ static pf_status sfail(pf_slabs* S, pf_status st, const std::string& m) {
 static long long halo_exchange_bytes(const pf_slabs* S, int which) {
     const pf_grid* g = S->s[0];
     const int nf = (has_th(g) ? 1 : 0) + (has_ph(g) ? 1 : 0);
-    const size_t esz = which < 2 ? fbytes(g) : sizeof(double);
+    const size_t esz = (which == 2 || which == 3) ? sizeof(double) : fbytes(g);
     return (long long)(S->P - 1) * 2 * nf * (long long)esz * S->n1 * S->n2;
 }
 
@@ -1592,7 +1601,7 @@ static cudaError_t halo(pf_slabs* S, int which, cudaStream_t st) {
     const long long plane = (long long)S->n1 * S->n2;
     const int fields = (has_th(g) ? 1 : 0) | (has_ph(g) ? 2 : 0);
     dim3 grid((unsigned)std::min<long long>((plane + 255) / 256, 1024), (unsigned)(4 * (S->P - 1)));
-    if (which >= 2 || !is_f32(g))
+    if (which == 2 || which == 3 || !is_f32(g))
         k_halo<double><<<grid, 256, 0, st>>>(S->d_tab, plane, which, fields, g->dctrl);
     else
         k_halo<float><<<grid, 256, 0, st>>>(S->d_tab, plane, which, fields, g->dctrl);
@@ -1609,6 +1618,7 @@ static cudaError_t slabs_enqueue_attempt(pf_slabs* S, cudaStream_t st) {
             if (e != cudaSuccess) return e;
         }
         cudaError_t e = halo(S, stage == 5 ? 2 : (stage % 2 == 1 ? 0 : 1), st);
+        if (e == cudaSuccess && stage == 1 && has_y32(S->s[0])) e = halo(S, 4, st);
         if (e != cudaSuccess) return e;
     }
     k_controller<<<1, 32, 0, st>>>(S->s[0]->dctrl);
@@ -1616,7 +1626,10 @@ static cudaError_t slabs_enqueue_attempt(pf_slabs* S, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-static long long slabs_attempt_launches(const pf_slabs* S) { return 5LL * (S->P + (S->P > 1 ? 1 : 0)) + 1; }
+static long long slabs_attempt_launches(const pf_slabs* S) {
+    const int extra = (S->P > 1 && has_y32(S->s[0])) ? 1 : 0;
+    return 5LL * (S->P + (S->P > 1 ? 1 : 0)) + extra + 1;
+}
 
 static void slabs_free_graph(pf_slabs* S) {
     if (S->graph) cudaGraphExecDestroy(S->graph);
@@ -1696,6 +1709,7 @@ pf_status pf_slabs_create(int n1, int n2, int n3, double h, int model, int react
         SlabTab& t = tab[q];
         t.f[0][0] = g->y_th[0]; t.f[0][1] = g->y_th[1]; t.f[0][2] = g->ua_th; t.f[0][3] = g->ub_th;
         t.f[1][0] = g->y_ph[0]; t.f[1][1] = g->y_ph[1]; t.f[1][2] = g->ua_ph; t.f[1][3] = g->ub_ph;
+        t.f[0][4] = g->y32_th; t.f[1][4] = g->y32_ph;
         t.n3 = g->n3;
         t.pad = 0;
     }
@@ -1829,6 +1843,7 @@ pf_status pf_slabs_run_to(pf_slabs* S, double t_end, double tol, long long max_s
     // unchanged planes)
     long long per_attempt = 0;
     for (int w : {0, 1, 0, 1, 2}) per_attempt += halo_exchange_bytes(S, w);
+    if (has_y32(S->s[0])) per_attempt += halo_exchange_bytes(S, 4);
     S->halo_bytes = replays * steps_per_graph * per_attempt;
     if (stats) {
         stats->n_accepted = c->n_acc;

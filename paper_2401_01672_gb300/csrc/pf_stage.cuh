@@ -26,14 +26,19 @@
 // Binary64 operation count: the binary64 pipe of sm_103a issues two FMAs per clock
 // per SM, a sixtieth of the binary32 rate, so the binary64 kernels keep every
 // comparison, absolute value and maximum in integer instructions on the IEEE bit
-// patterns, take blends as three FMAs, and divide with a Newton-Raphson reciprocal
+// patterns, take blends as three FMAs, and divide with one third-order reciprocal step
 // seeded by the binary32 reciprocal.
 //
 // Binary32 form (T = float): stage inputs chain from one stage input to the next
 // (u3 = u2 + dt/6 (k2 - k1), u4 = u2 - 5dt/24 k1 + 3dt/8 k3,
 // u5 = u4 + 3dt/8 k1 - 15dt/8 k3 + 2dt k4 -- algebraically the tableau rows) so that
 // only stages 1 and 5 touch the binary64 state; the state update y' = y + (dt/6 (k1 +
-// 4k4 + k5)) adds a binary32 increment to binary64 y.
+// 4k4 + k5)) adds a binary32 increment to binary64 y.  For the full model the chained quantities are
+// the increments d_s = u_s - y32 over a binary32 copy y32 of the state (written by stage 1), and the
+// stiff terms (heat flux, Laplacian) are formed from differences of y32 and of d_s separately: the
+// rounding of y to binary32 is then the same in every stage and drops out of the error estimate
+// (2 - 9 + 8 - 1 = 0), where rounding each u_s separately left a noise floor in E that the latent
+// heat (L/c ~ 160 K) lifts above usual tolerances, and the controller took several times more steps.
 #pragma once
 #include "pf_internal.cuh"
 #include <cfloat>
@@ -69,9 +74,11 @@ __device__ __forceinline__ bool lt_nonneg(float x, float y) { return x < y; }
 __device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }
 __device__ __forceinline__ bool positive(float x) { return x > 0.f; }
 
-// 1/x for x > 0: Newton-Raphson iteration r <- r + r (1 - x r), twice, from the binary32
-// reciprocal of x's leading 20 mantissa bits (relative error 2^-20 -> 2^-40 -> below 1 ulp).
-// The binary32 seed is built from the bit pattern with integer instructions.
+// 1/x for x > 0: from the binary32 reciprocal r of x's leading 20 mantissa bits (r = (1 + u)/x with
+// |u| < 2^-19.9), one third-order step r <- r + r (d + d^2), d = 1 - x r = -u: r (1 - u + u^2) =
+// (1 + u^3)/x, |u^3| < 2^-59, so the step's single final rounding leaves it within about half an ulp
+// (three binary64 FMAs where two Newton steps take four).  The binary32 seed is built from the bit
+// pattern with integer instructions.
 __device__ __forceinline__ double recip_pos(double x) {
     const long long b = __double_as_longlong(x);
     const int hi = (int)(b >> 32);
@@ -81,11 +88,8 @@ __device__ __forceinline__ double recip_pos(double x) {
     const int bf = __float_as_int(__frcp_rn(xf));
     const long long er = (long long)(((bf >> 23) & 0xFF) - 127 + 1023);
     double r = __longlong_as_double((er << 52) | ((long long)(bf & 0x7FFFFF) << 29));
-    double d = fma(-x, r, 1.0);
-    r = fma(r, d, r);
-    d = fma(-x, r, 1.0);
-    r = fma(r, d, r);
-    return r;
+    const double d = fma(-x, r, 1.0);
+    return fma(r, fma(d, d, d), r);
 }
 __device__ __forceinline__ float recip_pos(float x) { return __frcp_rn(x); }
 
@@ -204,6 +208,36 @@ __device__ __forceinline__ T allen_cahn_rate(const CoefT<T>& K, T pc, T pxm, T p
     return W * FMA(K.klap, lap, fh);
 }
 
+// The same rate at phi = a + d, where a is the cell's value in the binary32 copy of the state (common to
+// every stage of the step) and d the stage's increment, with the neighbours split the same way.  The
+// Laplacian, the gradient and the factor phi (1 - phi) are formed from differences of a and of d
+// separately: the rounding of a + d then enters only the limiter and the temperature factor, so the
+// stages' rates carry the same rounding of a (it cancels in the error estimate) instead of each its own.
+template <int RX, typename T>
+__device__ __forceinline__ T allen_cahn_rate_inc(const CoefT<T>& K, T a, T d, T axm, T axp, T aym, T ayp, T azm,
+                                                 T azp, T dxm, T dxp, T dym, T dyp, T dzm, T dzp, T th, T W) {
+    const T lap = FMA(T(-6), a, ((axm + axp) + (aym + ayp)) + (azm + azp)) +
+                  FMA(T(-6), d, ((dxm + dxp) + (dym + dyp)) + (dzm + dzp));
+    const T pc = a + d;
+    const T om = T(1) - pc;
+    // (a + d)(1 - a - d) = a (1 - a) + d (1 - 2a - d)
+    const T q = FMA(d, (T(1) - T(2) * a) - d, a * (T(1) - a));
+    T inner = (a - T(0.5)) + d;
+    T fh;
+    if constexpr (RX == R_GRADP) {
+        const T gx = (axp - axm) + (dxp - dxm), gy = (ayp - aym) + (dyp - dym), gz = (azp - azm) + (dzp - dzm);
+        const T gn = dsqrt(FMA(gx, gx, FMA(gy, gy, gz * gz)));
+        fh = FMA(q, inner, K.kgrad * gn * (-th));
+    } else {
+        if (!le_nonneg(pc, K.eps0) && !le_nonneg(om, K.eps0)) {
+            const T S = sigma_lim(pc, K) * sigma_lim(om, K);
+            inner = FMA(K.ksig * S, -th, inner);
+        }
+        fh = q * inner;
+    }
+    return W * FMA(K.klap, lap, fh);
+}
+
 // End of a tile: stage 5 folds the block's largest |2k1 - 9k3 + 8k4 - k5| into the error maximum (one
 // atomicMax on the binary64 bit pattern, scaled by dt/30); stage 1 adds the block's pore-bulk counts and
 // folds its largest |dphi/dt| (warp shuffles, then shared memory across the block's warps).
@@ -288,6 +322,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
     constexpr bool TEMP = (MODEL == M_TEMP);
     // full model in binary64: blends from precomputed per-cell coefficients (fewer binary64 operations)
     constexpr bool STATIC = (!F32 && MODEL == M_FULL);
+    // full model in binary32: the inputs of stages 2-5 are increments d = u - y32 over the binary32 copy
+    // y32 of the state that stage 1 writes; the heat flux, the Laplacian and phi (1 - phi) take the
+    // differences of y32 and of d separately (see allen_cahn_rate_inc)
+    constexpr bool INC = (F32 && MODEL == M_FULL);
+    constexpr bool DIN = (INC && STAGE >= 2);
 
     Ctrl* ctrl = a.ctrl;
     int cur = 0;
@@ -353,12 +392,25 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
         in_th = reinterpret_cast<const TIN*>(a.ub_th);
         in_ph = reinterpret_cast<const TIN*>(a.ub_ph);
     }
+    // increments: the stage buffer holds d, the values are read from y32
+    const T* in_dth = nullptr;
+    const T* in_dph = nullptr;
+    if constexpr (DIN) {
+        in_dth = reinterpret_cast<const T*>(in_th);
+        in_dph = reinterpret_cast<const T*>(in_ph);
+        in_th = reinterpret_cast<const TIN*>(a.y32_th);
+        in_ph = reinterpret_cast<const TIN*>(a.y32_ph);
+    }
     const T* __restrict__ Gf = a.G;
 
     constexpr int SX = TX + 2, SY = BY + 2;
-    __shared__ T s_th[HAS_TH ? 3 : 1][SY][SX];
-    __shared__ T s_ph[3][SY][SX];
+    // with increments, each cell's (y32, d) pair of a field sits in one 8-byte entry (one shared load)
+    constexpr bool TH1 = HAS_TH && !DIN;
+    __shared__ T s_th[TH1 ? 3 : 1][TH1 ? SY : 1][TH1 ? SX : 1];
+    __shared__ T s_ph[DIN ? 1 : 3][DIN ? 1 : SY][DIN ? 1 : SX];
     __shared__ T s_lam[HAS_TH ? 3 : 1][SY][SX];
+    __shared__ float2 s_th2[DIN ? 3 : 1][DIN ? SY : 1][DIN ? SX : 1];
+    __shared__ float2 s_ph2[DIN ? 3 : 1][DIN ? SY : 1][DIN ? SX : 1];
 
     // the per-cell coefficient arrays (64-bit offsets between arrays, computed once)
     const double* __restrict__ St = a.statics;
@@ -371,8 +423,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
     // raw loads of one cell of plane kk (clamped: mirror ghosts); G holds A_lam and B B_lam when STATIC
     // (theta and phi stay in the input type until `cvt`, so that a conversion does not wait for its
     // load where the load is issued)
-    auto fetch = [&](int kk, int off, TIN& th, TIN& ph, T& G, T& B) {
+    auto fetch = [&](int kk, int off, TIN& th, TIN& ph, T& G, T& B, T& dt, T& dp) {
         const int id = min(max(kk, a.cf.zlo), a.cf.zhi) * plane + off;
+        if constexpr (DIN) {
+            dt = in_dth[id];
+            dp = in_dph[id];
+        } else {
+            dt = T(0);
+            dp = T(0);
+        }
         if constexpr (STATIC) {
             G = T(St[id]);
             B = T(St_B[id]);
@@ -391,27 +450,56 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
         if constexpr (HAS_PH) ph = to_T<T>(rph);
         else ph = T(0);
     };
-    auto fetch_cvt = [&](int kk, int off, T& th, T& ph, T& G, T& B) {
+    auto fetch_cvt = [&](int kk, int off, T& th, T& ph, T& G, T& B, T& dt, T& dp) {
         TIN rth, rph;
-        fetch(kk, off, rth, rph, G, B);
+        fetch(kk, off, rth, rph, G, B, dt, dp);
         cvt(rth, rph, th, ph);
     };
-    // derived values: Temp phase field (eq. explicit-p-dependence-on-T) and blended conductivity
-    auto finish = [&](T th, T& ph, T G, T B, T& lam, T& tg) {
+    // derived values: Temp phase field (eq. explicit-p-dependence-on-T) and blended conductivity (at
+    // phi = y32 + d with increments)
+    auto finish = [&](T th, T& ph, T G, T B, T& lam, T& tg, T dp) {
         if constexpr (TEMP) {
             tg = dtanh(K.gamma * th);
             ph = T(0.5) * water_ind(G, K.zeta) * (T(1) - tg);
         }
         if constexpr (STATIC) lam = FMA(ph, B, G);
+        else if constexpr (DIN) lam = blend3(G, ph + dp, K.lamL, K.dLG, K.dLI);
         else if constexpr (HAS_TH) lam = blend3(G, ph, K.lamL, K.dLG, K.dLI);
         else lam = T(0);
     };
-    auto put = [&](int b, int y, int x, T th, T ph, T lam) {
-        if constexpr (HAS_TH) {
-            s_th[b][y][x] = th;
+    auto put = [&](int b, int y, int x, T th, T ph, T lam, T dt, T dp) {
+        if constexpr (DIN) {
+            s_th2[b][y][x] = make_float2(th, dt);
+            s_ph2[b][y][x] = make_float2(ph, dp);
             s_lam[b][y][x] = lam;
+        } else {
+            if constexpr (HAS_TH) {
+                s_th[b][y][x] = th;
+                s_lam[b][y][x] = lam;
+            }
+            s_ph[b][y][x] = ph;
         }
-        s_ph[b][y][x] = ph;
+    };
+    // a lateral neighbour of plane b: value and (with increments) increment
+    auto nb_th = [&](int bb, int yy, int xx, T& v, T& d) {
+        if constexpr (DIN) {
+            const float2 q = s_th2[bb][yy][xx];
+            v = q.x;
+            d = q.y;
+        } else {
+            v = s_th[bb][yy][xx];
+            d = T(0);
+        }
+    };
+    auto nb_ph = [&](int bb, int yy, int xx, T& v, T& d) {
+        if constexpr (DIN) {
+            const float2 q = s_ph2[bb][yy][xx];
+            v = q.x;
+            d = q.y;
+        } else {
+            v = s_ph[bb][yy][xx];
+            d = T(0);
+        }
     };
 
     auto ac_rate = [&](T pc, T pxm, T pxp, T pym, T pyp, T pzm, T pzp, T th, T W) -> T {
@@ -455,27 +543,27 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
     }
 
     // ---- prologue: own column at kb-1, kb, kb+1; planes kb, kb+1 into the ring
-    T thm, phm, lamm, tgm = T(0);
-    T thc, phc, lamc, Gc, tgc = T(0);
-    T thp, php, lamp, Gp, tgp = T(0);
+    T thm, phm, lamm, tgm = T(0), dtm, dpm;
+    T thc, phc, lamc, Gc, tgc = T(0), dtc, dpc;
+    T thp, php, lamp, Gp, tgp = T(0), dtp, dpp;
     {
         T Gm, Bm, Bc, Bp;
-        fetch_cvt(kb - 1, ooff, thm, phm, Gm, Bm);
-        finish(thm, phm, Gm, Bm, lamm, tgm);
-        fetch_cvt(kb, ooff, thc, phc, Gc, Bc);
-        finish(thc, phc, Gc, Bc, lamc, tgc);
-        put(0, ty + 1, tx + 1, thc, phc, lamc);
-        fetch_cvt(kb + 1, ooff, thp, php, Gp, Bp);
-        finish(thp, php, Gp, Bp, lamp, tgp);
-        put(1, ty + 1, tx + 1, thp, php, lamp);
+        fetch_cvt(kb - 1, ooff, thm, phm, Gm, Bm, dtm, dpm);
+        finish(thm, phm, Gm, Bm, lamm, tgm, dpm);
+        fetch_cvt(kb, ooff, thc, phc, Gc, Bc, dtc, dpc);
+        finish(thc, phc, Gc, Bc, lamc, tgc, dpc);
+        put(0, ty + 1, tx + 1, thc, phc, lamc, dtc, dpc);
+        fetch_cvt(kb + 1, ooff, thp, php, Gp, Bp, dtp, dpp);
+        finish(thp, php, Gp, Bp, lamp, tgp, dpp);
+        put(1, ty + 1, tx + 1, thp, php, lamp, dtp, dpp);
         if (hal) {
-            T h_th, h_ph, h_G, h_B, h_lam, h_tg;
-            fetch_cvt(kb, hoff, h_th, h_ph, h_G, h_B);
-            finish(h_th, h_ph, h_G, h_B, h_lam, h_tg);
-            put(0, hy + 1, hx + 1, h_th, h_ph, h_lam);
-            fetch_cvt(kb + 1, hoff, h_th, h_ph, h_G, h_B);
-            finish(h_th, h_ph, h_G, h_B, h_lam, h_tg);
-            put(1, hy + 1, hx + 1, h_th, h_ph, h_lam);
+            T h_th, h_ph, h_G, h_B, h_lam, h_tg, h_dt, h_dp;
+            fetch_cvt(kb, hoff, h_th, h_ph, h_G, h_B, h_dt, h_dp);
+            finish(h_th, h_ph, h_G, h_B, h_lam, h_tg, h_dp);
+            put(0, hy + 1, hx + 1, h_th, h_ph, h_lam, h_dt, h_dp);
+            fetch_cvt(kb + 1, hoff, h_th, h_ph, h_G, h_B, h_dt, h_dp);
+            finish(h_th, h_ph, h_G, h_B, h_lam, h_tg, h_dp);
+            put(1, hy + 1, hx + 1, h_th, h_ph, h_lam, h_dt, h_dp);
         }
     }
     __syncthreads();
@@ -489,9 +577,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
     for (int k = kb; k < ke; ++k) {
         // 1. raw values of plane k+2 (consumed after the arithmetic of plane k)
         TIN rth, rph, qth, qph;
-        T rG, rB, qG, qB;
-        fetch(k + 2, ooff, rth, rph, rG, rB);
-        if (hal) fetch(k + 2, hoff, qth, qph, qG, qB);
+        T rG, rB, qG, qB, rdt, rdp, qdt, qdp;
+        fetch(k + 2, ooff, rth, rph, rG, rB, rdt, rdp);
+        if (hal) fetch(k + 2, hoff, qth, qph, qG, qB, qdt, qdp);
 
         const int id = k * plane + j * n1 + i;
         // phase field of the lateral neighbours (Laplacian, gradient) and the bulk test
@@ -562,33 +650,48 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
         T div = T(0);
         if (inside) {
             if constexpr (MODEL != M_MICRO) {
-                const T t_xm = s_th[b][ty + 1][tx], t_xp = s_th[b][ty + 1][tx + 2];
-                const T t_ym = s_th[b][ty][tx + 1], t_yp = s_th[b][ty + 2][tx + 1];
+                T t_xm, t_xp, t_ym, t_yp, d_xm, d_xp, d_ym, d_yp;
+                nb_th(b, ty + 1, tx, t_xm, d_xm);
+                nb_th(b, ty + 1, tx + 2, t_xp, d_xp);
+                nb_th(b, ty, tx + 1, t_ym, d_ym);
+                nb_th(b, ty + 2, tx + 1, t_yp, d_yp);
                 const T l_xm = s_lam[b][ty + 1][tx], l_xp = s_lam[b][ty + 1][tx + 2];
                 const T l_ym = s_lam[b][ty][tx + 1], l_yp = s_lam[b][ty + 2][tx + 1];
+                // theta_j - theta_c; with increments (y32_j - y32_c) + (d_j - d_c)
+                T g_xm = t_xm - thc, g_xp = t_xp - thc, g_ym = t_ym - thc, g_yp = t_yp - thc;
+                T g_zm = thm - thc, g_zp = thp - thc, g_b = th_b - thc;
+                if constexpr (DIN) {
+                    g_xm += d_xm - dtc;
+                    g_xp += d_xp - dtc;
+                    g_ym += d_ym - dtc;
+                    g_yp += d_yp - dtc;
+                    g_zm += dtm - dtc;
+                    g_zp += dtp - dtc;
+                    g_b -= dtc;
+                }
                 if (!a.cf.harmonic) {
-                    div = (lamc + l_xm) * (t_xm - thc);
-                    div = FMA(lamc + l_xp, t_xp - thc, div);
-                    div = FMA(lamc + l_ym, t_ym - thc, div);
-                    div = FMA(lamc + l_yp, t_yp - thc, div);
-                    div = FMA(lamc + lamm, thm - thc, div);
-                    div = FMA(lamc + lamp, thp - thc, div);
+                    div = (lamc + l_xm) * g_xm;
+                    div = FMA(lamc + l_xp, g_xp, div);
+                    div = FMA(lamc + l_ym, g_ym, div);
+                    div = FMA(lamc + l_yp, g_yp, div);
+                    div = FMA(lamc + lamm, g_zm, div);
+                    div = FMA(lamc + lamp, g_zp, div);
                 } else {
                     auto hm = [&](T lj) {
                         const T s = lamc + lj;
                         return positive(s) ? T(4) * lamc * lj / s : T(0);
                     };
-                    div = hm(l_xm) * (t_xm - thc);
-                    div = FMA(hm(l_xp), t_xp - thc, div);
-                    div = FMA(hm(l_ym), t_ym - thc, div);
-                    div = FMA(hm(l_yp), t_yp - thc, div);
-                    div = FMA(hm(lamm), thm - thc, div);
-                    div = FMA(hm(lamp), thp - thc, div);
+                    div = hm(l_xm) * g_xm;
+                    div = FMA(hm(l_xp), g_xp, div);
+                    div = FMA(hm(l_ym), g_ym, div);
+                    div = FMA(hm(l_yp), g_yp, div);
+                    div = FMA(hm(lamm), g_zm, div);
+                    div = FMA(hm(lamp), g_zp, div);
                 }
                 if (dmask) {
                     const int nd = nd_xy + ((dmask & 16) && k == 0) + ((dmask & 32) && k == n3 - 1);
                     // Dirichlet face: 2 lambda (theta_b - theta)/h^2 = 4 lambda' (theta_b - theta)
-                    if (nd) div = FMA(T(4 * nd) * lamc, th_b - thc, div);
+                    if (nd) div = FMA(T(4 * nd) * lamc, g_b, div);
                 }
             }
         }
@@ -637,11 +740,18 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
                 __syncthreads();
                 if (need) dph = s_slot[0][slot];
             } else if (need) {
+                T q_xm = T(0), q_xp = T(0), q_ym = T(0), q_yp = T(0);
                 if constexpr (F32) {
-                    p_xm = s_ph[b][ty + 1][tx]; p_xp = s_ph[b][ty + 1][tx + 2];
-                    p_ym = s_ph[b][ty][tx + 1]; p_yp = s_ph[b][ty + 2][tx + 1];
+                    nb_ph(b, ty + 1, tx, p_xm, q_xm);
+                    nb_ph(b, ty + 1, tx + 2, p_xp, q_xp);
+                    nb_ph(b, ty, tx + 1, p_ym, q_ym);
+                    nb_ph(b, ty + 2, tx + 1, p_yp, q_yp);
                 }
-                dph = ac_rate(phc, p_xm, p_xp, p_ym, p_yp, phm, php, thc, W);
+                if constexpr (DIN)
+                    dph = allen_cahn_rate_inc<RX>(K, phc, dpc, p_xm, p_xp, p_ym, p_yp, phm, php, q_xm, q_xp, q_ym, q_yp,
+                                                  dpm, dpp, thc + dtc, W);
+                else
+                    dph = ac_rate(phc, p_xm, p_xp, p_ym, p_yp, phm, php, thc, W);
             }
         }
         if (inside) {
@@ -655,8 +765,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
                     dth = FMA(FMA(phc, sD1, sD0), dph, div) * recip_pos(rhoc);
                 }
             } else if constexpr (MODEL == M_FULL) {
-                const T rho = blend3(Gc, phc, K.rhoL, K.dRG, K.dRI);
-                const T cp = blend3(Gc, phc, K.capL, K.dCG, K.dCI);
+                const T phu = DIN ? phc + dpc : phc;
+                const T rho = blend3(Gc, phu, K.rhoL, K.dRG, K.dRI);
+                const T cp = blend3(Gc, phu, K.capL, K.dCG, K.dCI);
                 dth = FMA(rho * K.latent, dph, div) * recip_pos(rho * cp);
             } else if constexpr (TEMP) {
                 const T rho = blend3(Gc, phc, K.rhoL, K.dRG, K.dRI);
@@ -666,15 +777,25 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
                 dph = dp * dth;
             }
 
-            // ---- fused stage combination
+            // ---- fused stage combination (binary32 stages 2 and 4 continue from their own input: the
+            // increment with increments, else the stage value)
+            const T bth = DIN ? dtc : thc, bph = DIN ? dpc : phc;
             if constexpr (STAGE == 0) {
                 if (a.out_th) a.out_th[id] = dth;
                 if (a.out_ph) a.out_ph[id] = dph;
             } else if constexpr (STAGE == 1) {
-                if constexpr (HAS_TH) { a.k1_th[id] = dth; a.ua_th[id] = FMA(sc[0], dth, thc); }
-                if constexpr (HAS_PH) {
+                if constexpr (INC) {
+                    a.y32_th[id] = thc;
+                    a.y32_ph[id] = phc;
+                    a.k1_th[id] = dth;
+                    a.ua_th[id] = sc[0] * dth;
                     a.k1_ph[id] = dph;
-                    a.ua_ph[id] = FMA(sc[0], dph, phc);
+                    a.ua_ph[id] = sc[0] * dph;
+                } else {
+                    if constexpr (HAS_TH) { a.k1_th[id] = dth; a.ua_th[id] = FMA(sc[0], dth, thc); }
+                    if constexpr (HAS_PH) { a.k1_ph[id] = dph; a.ua_ph[id] = FMA(sc[0], dph, phc); }
+                }
+                if constexpr (HAS_PH) {
                     // ice and cell counts of the pore bulk (I_W > 1/2) for the equilibrium test
                     bool in_pore;
                     if constexpr (STATIC) in_pore = ge_nonneg(sW, K.wa_half) && sW != K.wa_half;
@@ -688,8 +809,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
                 }
             } else if constexpr (STAGE == 2) {
                 if constexpr (F32) {
-                    if constexpr (HAS_TH) a.ub_th[id] = FMA(sc[1], dth - k1t, thc);
-                    if constexpr (HAS_PH) a.ub_ph[id] = FMA(sc[1], dph - k1p, phc);
+                    if constexpr (HAS_TH) a.ub_th[id] = FMA(sc[1], dth - k1t, bth);
+                    if constexpr (HAS_PH) a.ub_ph[id] = FMA(sc[1], dph - k1p, bph);
                 } else {
                     if constexpr (HAS_TH) a.ub_th[id] = FMA(sc[1], k1t + dth, y_t);
                     if constexpr (HAS_PH) a.ub_ph[id] = FMA(sc[1], k1p + dph, y_p);
@@ -704,8 +825,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
                 }
             } else if constexpr (STAGE == 4) {
                 if constexpr (F32) {
-                    if constexpr (HAS_TH) { a.k4_th[id] = dth; a.ub_th[id] = FMA(sc[6], dth, FMA(-sc[9], k3t, FMA(sc[3], k1t, thc))); }
-                    if constexpr (HAS_PH) { a.k4_ph[id] = dph; a.ub_ph[id] = FMA(sc[6], dph, FMA(-sc[9], k3p, FMA(sc[3], k1p, phc))); }
+                    if constexpr (HAS_TH) { a.k4_th[id] = dth; a.ub_th[id] = FMA(sc[6], dth, FMA(-sc[9], k3t, FMA(sc[3], k1t, bth))); }
+                    if constexpr (HAS_PH) { a.k4_ph[id] = dph; a.ub_ph[id] = FMA(sc[6], dph, FMA(-sc[9], k3p, FMA(sc[3], k1p, bph))); }
                 } else {
                     if constexpr (HAS_TH) { a.k4_th[id] = dth; a.ub_th[id] = FMA(sc[6], dth, FMA(-sc[5], k3t, FMA(sc[4], k1t, y_t))); }
                     if constexpr (HAS_PH) { a.k4_ph[id] = dph; a.ub_ph[id] = FMA(sc[6], dph, FMA(-sc[5], k3p, FMA(sc[4], k1p, y_p))); }
@@ -733,17 +854,17 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
         {
             T cth, cph, lam2, tg2 = T(0);
             cvt(rth, rph, cth, cph);
-            finish(cth, cph, rG, rB, lam2, tg2);
-            put(b2, ty + 1, tx + 1, cth, cph, lam2);
-            thm = thc; phm = phc; lamm = lamc; tgm = tgc;
-            thc = thp; phc = php; lamc = lamp; Gc = Gp; tgc = tgp;
-            thp = cth; php = cph; lamp = lam2; Gp = rG; tgp = tg2;
+            finish(cth, cph, rG, rB, lam2, tg2, rdp);
+            put(b2, ty + 1, tx + 1, cth, cph, lam2, rdt, rdp);
+            thm = thc; phm = phc; lamm = lamc; tgm = tgc; dtm = dtc; dpm = dpc;
+            thc = thp; phc = php; lamc = lamp; Gc = Gp; tgc = tgp; dtc = dtp; dpc = dpp;
+            thp = cth; php = cph; lamp = lam2; Gp = rG; tgp = tg2; dtp = rdt; dpp = rdp;
         }
         if (hal) {
             T h_th, h_ph, h_lam, h_tg;
             cvt(qth, qph, h_th, h_ph);
-            finish(h_th, h_ph, qG, qB, h_lam, h_tg);
-            put(b2, hy + 1, hx + 1, h_th, h_ph, h_lam);
+            finish(h_th, h_ph, qG, qB, h_lam, h_tg, qdp);
+            put(b2, hy + 1, hx + 1, h_th, h_ph, h_lam, qdt, qdp);
         }
         b = (b + 1) % 3;
         __syncthreads();

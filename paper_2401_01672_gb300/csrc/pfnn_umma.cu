@@ -296,6 +296,244 @@ k_conv_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
 }
 
+// ---------------------------------------------------------------- narrow layers: one halo tile per brick
+// For 16 or 32 channels the per-tap boxes of k_conv_umma are 32- or 64-byte rows and the 27 boxes of a
+// 128-voxel tile move 27 times its input through TMA.  Here a block loads the input of its whole brick
+// (8 x 16 x DZ cells, x fastest) once, with a one-cell halo: a (DZ + 2) x 18 x 10 tile per 8-channel
+// chunk, unswizzled, so that every cell is a 16-byte row and a row of 10 cells is 160 contiguous bytes.  The A
+// operand of one tap is then a window of that tile: for output plane zo and tap (dz, dy, dx), the 128 rows
+// (8 x by 16 y) start at cell (dx + 1, dy + 1, zo + dz + 1) of the tile; 8 consecutive x cells are one
+// 8 x 16-byte core matrix, consecutive y rows are 160 bytes apart (the stride between core matrices along
+// M) and consecutive 8-channel chunks one chunk apart (the stride along K).  The descriptor start is a
+// multiple of 16 bytes, as the unswizzled layout requires.  The weights of all 27 taps stay in shared
+// memory in the same core-matrix layout: [tap][chunk][cout][8 channels].  Per brick: DZ x 27 x cin/16 MMAs
+// (M = 128, N = cout, K = 16) into DZ accumulators of cout columns each.
+struct HaloArgs {
+    int cin, cout, dz_planes;     // channels in/out, output planes per brick
+    int D, H, W;                  // grid of one sample
+    int tx, ty, tz;               // bricks per sample
+    int flip, relu, accumulate;
+    int withhold;                 // >= 0: the tile loads are withheld (failure-path test)
+    long long tries;
+    unsigned chunk_bytes;         // shared bytes of one 8-channel chunk of the tile (1024-byte multiple)
+    unsigned tile_bytes;          // all chunks
+    unsigned w_bytes;             // weights of all taps
+    unsigned tx_bytes;            // bytes the tile loads deliver
+    unsigned idesc;
+    int tmem_cols;
+    const float* bias;
+    const bf16* w;
+    bf16* y;
+    float* yf;
+    int ldy, yoff;
+};
+
+constexpr int HB_X = 8, HB_Y = 16;            // brick extent along x and y (one plane = 128 voxels)
+constexpr int HT_X = HB_X + 2, HT_Y = HB_Y + 2;
+constexpr unsigned HT_ROW = HT_X * 16;        // bytes of one tile row of 8 channels
+
+// unswizzled K-major descriptor: start, stride along K (LBO) and along M/N (SBO), version 1
+__device__ __forceinline__ uint64_t desc_plain(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ULL << 46);
+}
+
+// tcgen05.mma with the descriptors given as 32-bit words (the issue loop advances the low words only)
+__device__ __forceinline__ void umma_f16_w(uint32_t tmem_d, uint32_t alo, uint32_t ahi, uint32_t blo, uint32_t bhi,
+                                           uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
+        "setp.ne.b32 p, %6, 0;\n\t"
+        "mov.b64 da, {%1, %2};\n\t"
+        "mov.b64 db, {%3, %4};\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n\t}" ::"r"(tmem_d),
+        "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// The MMAs of one brick.  a_lo / b_lo: low descriptor words of the tile and weight bases; the start field
+// (bits 0-13, 16-byte units) is advanced by adding to the low word (the shared window lies below 256 KB,
+// so it never carries out).  Tap t = 9 (dz + 1) + 3 (dy + 1) + (dx + 1) reads the window at tile cell
+// (dx + 1, dy + 1, zo + dz + 1); flipped taps (backward data) read the window of tap 26 - t.
+template <bool FLIP, int NKB>
+__device__ __forceinline__ void halo_issue(uint32_t tmem, uint32_t a_lo, uint32_t a_hi, uint32_t b_lo, uint32_t b_hi,
+                                           uint32_t idesc, int planes, int cout, uint32_t chunk16) {
+#pragma unroll
+    for (int t = 0; t < 27; ++t) {
+        const int u = FLIP ? 26 - t : t;
+        const uint32_t off = (uint32_t)(((u / 9) * HT_Y + (u / 3) % 3) * HT_X + u % 3);
+#pragma unroll
+        for (int kb = 0; kb < NKB; ++kb) {
+            const uint32_t a_t = a_lo + off + (uint32_t)(2 * kb) * chunk16;
+            const uint32_t b_t = b_lo + (uint32_t)((t * 2 * NKB + 2 * kb) * cout);
+            const uint32_t accf = (t > 0 || kb > 0) ? 1u : 0u;
+            // output plane zo: its accumulator, the window one tile plane further
+            for (int zo = 0; zo < planes; ++zo)
+                umma_f16_w(tmem + (uint32_t)(zo * cout), a_t + (uint32_t)(zo * HT_Y * HT_X), a_hi, b_t, b_hi, idesc,
+                           accf);
+        }
+    }
+}
+
+// Weights of all taps into shared memory as [tap][chunk][cout][8], in rounds of 7 16-byte vectors per
+// thread: each round loads all of its vectors (read-only path) before storing them, so the copy costs one
+// round trip to L2 per 14 KB (one for 16 x 16 channels, four for 32 x 32).
+__device__ __forceinline__ void halo_weights(const bf16* __restrict__ w, unsigned char* dst, int cout, int nkc) {
+    constexpr int CAP = 7;
+    const int nvec = 27 * cout * nkc;
+    const uint4* src = reinterpret_cast<const uint4*>(w);
+    for (int base = 0; base < nvec; base += CAP * UTHR) {
+        uint4 v[CAP];
+#pragma unroll
+        for (int j = 0; j < CAP; ++j) {
+            const int q = base + threadIdx.x + j * UTHR;
+            if (q < nvec) v[j] = __ldg(src + q);
+        }
+#pragma unroll
+        for (int j = 0; j < CAP; ++j) {
+            const int q = base + threadIdx.x + j * UTHR;
+            if (q < nvec) {
+                const int kc = q % nkc;
+                const int co = (q / nkc) % cout;
+                const int t = q / (nkc * cout);
+                *reinterpret_cast<uint4*>(dst + ((size_t)(t * nkc + kc) * cout + co) * 16) = v[j];
+            }
+        }
+    }
+}
+
+// One block per brick: thread 0 issues the tile's TMA loads (one box per 8-channel chunk, zero fill
+// outside the grid) while all threads copy the weights; thread 32 issues the MMAs once the tile has
+// landed and commits them to one barrier; all four warps read the accumulators (bias and ReLU applied
+// from registers).  Three or two blocks share an SM (shared memory), so one block's loads overlap
+// another's MMAs and epilogue.  Both waits are bounded.
+__global__ void __launch_bounds__(UTHR)
+k_conv_halo(const __grid_constant__ CUtensorMap tmX, const HaloArgs p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    unsigned char* ctl = sm + p.tile_bytes + p.w_bytes;
+    const uint32_t full = smem_u32(ctl);
+    const uint32_t accum = full + 8u;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ctl + 16);
+    __shared__ int s_fail;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nkc = p.cin / 8;
+    long long b = blockIdx.x;
+    const int bx = (int)(b % p.tx);
+    b /= p.tx;
+    const int by = (int)(b % p.ty);
+    b /= p.ty;
+    const int bz = (int)(b % p.tz);
+    const int bn = (int)(b / p.tz);
+    const int x0 = bx * HB_X, y0 = by * HB_Y, z0 = bz * p.dz_planes;
+    const uint32_t tile0 = smem_u32(sm);
+    const uint32_t w0 = tile0 + p.tile_bytes;
+
+    if (threadIdx.x == 0) {
+        mbar_init(full, 1);
+        mbar_init(accum, 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_expect_tx(full, p.tx_bytes);
+        if (p.withhold < 0) {  // failure-path test: the tile never arrives
+            for (int kc = 0; kc < nkc; ++kc)
+                tma_load_5d(tile0 + (uint32_t)kc * p.chunk_bytes, &tmX, full, kc * 8, x0 - 1, y0 - 1, z0 - 1, bn);
+        }
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(p.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    halo_weights(p.w, sm + p.tile_bytes, p.cout, nkc);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (threadIdx.x == 32) {
+        const bool ok = mbar_wait(full, 0u, p.tries);
+        if (ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint64_t da = desc_plain(tile0, p.chunk_bytes, HT_ROW);
+            const uint64_t db = desc_plain(w0, (uint32_t)p.cout * 16u, 128u);
+            const uint32_t alo = (uint32_t)da, ahi = (uint32_t)(da >> 32), blo = (uint32_t)db, bhi = (uint32_t)(db >> 32);
+            const uint32_t c16 = p.chunk_bytes >> 4;
+            if (p.flip) {
+                if (nkc == 2) halo_issue<true, 1>(tmem, alo, ahi, blo, bhi, p.idesc, p.dz_planes, p.cout, c16);
+                else halo_issue<true, 2>(tmem, alo, ahi, blo, bhi, p.idesc, p.dz_planes, p.cout, c16);
+            } else {
+                if (nkc == 2) halo_issue<false, 1>(tmem, alo, ahi, blo, bhi, p.idesc, p.dz_planes, p.cout, c16);
+                else halo_issue<false, 2>(tmem, alo, ahi, blo, bhi, p.idesc, p.dz_planes, p.cout, c16);
+            }
+        } else {
+            s_fail = 1;
+        }
+        umma_commit(accum);  // also after a failed wait: every issued MMA has retired when it completes
+    }
+    __syncwarp();
+    __syncthreads();
+
+    const bool ready = mbar_wait(accum, 0u, p.tries) && !s_fail;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int m = warp * 32 + lane;           // accumulator row: x = m % 8, y = m / 8
+    const int x = x0 + (m % HB_X), y = y0 + m / HB_X;
+    const bool inxy = ready && x < p.W && y < p.H;
+    for (int c0 = 0; c0 < p.cout; c0 += 16) {
+        float bias[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) bias[q] = p.bias ? __ldg(p.bias + c0 + q) : 0.f;
+        for (int zo = 0; zo < p.dz_planes; ++zo) {
+            const int z = z0 + zo;
+            const bool inside = inxy && z < p.D;
+            const long long v = (((long long)bn * p.D + z) * p.H + y) * p.W + x;
+            float o[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(zo * p.cout + c0), o);  // whole warp
+            if (!inside) continue;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) o[q] += bias[q];
+            if (p.relu) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) o[q] = fmaxf(o[q], 0.f);
+            }
+            if (p.yf) {
+                float4* dst = reinterpret_cast<float4*>(p.yf + v * p.ldy + p.yoff + c0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float4 w = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+                    if (p.accumulate) {
+                        const float4 r = dst[q];
+                        w.x += r.x; w.y += r.y; w.z += r.z; w.w += r.w;
+                    }
+                    dst[q] = w;
+                }
+            } else {
+                uint4 pk[2];
+                uint32_t* u = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(o[2 * q], o[2 * q + 1]);
+                    u[q] = *reinterpret_cast<const uint32_t*>(&h2);
+                }
+                uint4* dst = reinterpret_cast<uint4*>(p.y + v * p.ldy + p.yoff + c0);
+                dst[0] = pk[0];
+                dst[1] = pk[1];
+            }
+        }
+    }
+    // a tile load still in flight after a failed wait lands before the shared memory is released
+    if (threadIdx.x == 0 && !ready && p.withhold < 0) mbar_wait(full, 0u, p.tries);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 2) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
+    }
+}
+
 // ---------------------------------------------------------------- weight gradient on tcgen05
 // dW[t][co][ci] = sum over voxels v of dY[v][co] X[v + off(t)][ci] (zero padding) is, with u = v + off(t),
 // sum over u of dY[u - off(t)][co] X[u][ci]: a GEMM whose reduction runs over voxels.  Both tensors are
@@ -478,6 +716,72 @@ unsigned long long umma_layout(int ck) { return ck == 16 ? 6ULL : (ck == 32 ? 4U
 
 unsigned round1024(unsigned v) { return (v + 1023u) & ~1023u; }
 
+// the narrow-layer kernel takes 16 or 32 channels in and out on grids at least one brick across
+bool halo_shape(int cin, int cout, int d, int h, int wd) {
+    return (cin == 16 || cin == 32) && (cout == 16 || cout == 32) && wd >= HB_X && h >= HB_Y && d >= 4;
+}
+
+pf_status conv_halo(const void* x, int ldx, int xoff, const void* w, int cin, int cout, const float* bias, int relu,
+                    int flip, void* y_bf16, float* y_f32, int ldy, int yoff, int accumulate, int n, int d, int h,
+                    int wd, cudaStream_t stream, PFN_cuTensorMapEncodeTiled_v12000 enc) {
+    HaloArgs a{};
+    a.cin = cin;
+    a.cout = cout;
+    a.D = d;
+    a.H = h;
+    a.W = wd;
+    a.flip = flip;
+    a.relu = relu;
+    a.accumulate = accumulate;
+    a.withhold = g_test_withhold;
+    a.tries = g_test_tries > 0 ? g_test_tries : WAIT_TRIES;
+    g_test_withhold = -1;
+    g_test_tries = 0;
+    a.w_bytes = (unsigned)(27 * cout * cin * 2);
+    // 8 output planes per brick where the tile and the weights leave room for two blocks per SM, else 4
+    int dzp = 8;
+    auto chunk = [](int dz) { return round1024((unsigned)(HT_ROW * HT_Y * (dz + 2))); };
+    if ((size_t)(cin / 8) * chunk(8) + a.w_bytes > 110u * 1024u) dzp = 4;
+    a.dz_planes = dzp;
+    a.chunk_bytes = chunk(dzp);
+    a.tile_bytes = (unsigned)(cin / 8) * a.chunk_bytes;
+    a.tx_bytes = (unsigned)(cin / 8) * (HT_ROW * HT_Y * (dzp + 2));
+    a.tx = (wd + HB_X - 1) / HB_X;
+    a.ty = (h + HB_Y - 1) / HB_Y;
+    a.tz = (d + dzp - 1) / dzp;
+    a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(cout >> 3) << 17) | ((unsigned)(UM >> 4) << 24);
+    const int cols = dzp * cout;
+    a.tmem_cols = cols <= 32 ? 32 : (cols <= 64 ? 64 : (cols <= 128 ? 128 : 256));
+    a.bias = bias;
+    a.w = (const bf16*)w;
+    a.y = (bf16*)y_bf16;
+    a.yf = y_f32;
+    a.ldy = ldy;
+    a.yoff = yoff;
+    alignas(64) CUtensorMap mX;
+    const cuuint64_t dims[5] = {(cuuint64_t)cin, (cuuint64_t)wd, (cuuint64_t)h, (cuuint64_t)d, (cuuint64_t)n};
+    const cuuint64_t row = (cuuint64_t)ldx * 2;
+    const cuuint64_t strides[4] = {row, row * wd, row * wd * h, row * wd * h * d};
+    const cuuint32_t box[5] = {8, (cuuint32_t)HT_X, (cuuint32_t)HT_Y, (cuuint32_t)(dzp + 2), 1};
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    if (enc(&mX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)((const bf16*)x + xoff), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return PF_E_INVALID;
+    const size_t smem = 1024 + (size_t)a.tile_bytes + a.w_bytes + 32;
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_err = cudaFuncSetAttribute(k_conv_halo, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    });
+    if (attr_err != cudaSuccess || smem > 200u * 1024u) return PF_E_CUDA;
+    const long long blocks = (long long)a.tx * a.ty * a.tz * n;
+    if (blocks > 0x7FFFFFFFLL) return PF_E_RANGE;
+    k_conv_halo<<<(unsigned)blocks, UTHR, smem, stream>>>(mX, a);
+    pfgb::count_launch();
+    return cudaGetLastError() == cudaSuccess ? PF_OK : PF_E_CUDA;
+}
+
 }  // namespace
 
 extern "C" {
@@ -494,6 +798,9 @@ pf_status pfnn_conv3d(const void* x, int ldx, int xoff, const void* w, int cin, 
         return PF_E_INVALID;
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return PF_E_CUDA;
+    if (halo_shape(cin, cout, d, h, wd))
+        return conv_halo(x, ldx, xoff, w, cin, cout, bias, relu, flip, y_bf16, y_f32, ldy, yoff, accumulate, n, d, h,
+                         wd, (cudaStream_t)stream, enc);
 
     UmmaArgs a{};
     a.cin = cin;

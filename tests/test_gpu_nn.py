@@ -72,6 +72,79 @@ def test_conv_forward(env, cin, cout, shape):
     assert no_failed_waits(nn)
 
 
+# narrow layers (16 or 32 channels in and out, grids at least 8 x 16 x 4) take the halo-tile kernel: one
+# input tile per 8 x 16 x 4-or-8 brick, tap windows addressed in shared memory, one block per SM walking
+# the bricks through two tile buffers and two accumulators; ragged in every direction, and one grid with
+# several bricks per block (2 x 32 x 96 x 96: 576 or 1152 bricks on 152 blocks)
+HALO_SHAPES = [(1, 5, 17, 12), (2, 8, 16, 8), (1, 9, 33, 21), (2, 32, 96, 96)]
+
+
+@pytest.mark.parametrize("shape", HALO_SHAPES)
+@pytest.mark.parametrize("cin,cout", [(16, 16), (16, 32), (32, 16), (32, 32)])
+def test_conv_halo_tile_kernel(env, cin, cout, shape):
+    """Forward (bias, ReLU, bf16 and fp32 outputs, channel slices of wider buffers) and backward data
+    (flipped taps, transposed weights, accumulation into a non-zero fp32 gradient) against the oracle."""
+    torch, nn, O = env
+    L = nn._lib()
+    g = np.random.default_rng(cin * 5 + cout + shape[2])
+    n, d, h, w = shape
+    big = g.standard_normal((n, d, h, w, cin + 16))                  # input slice [8, 8 + cin)
+    bt, bv = bf(torch, big)
+    x = bv[..., 8:8 + cin]
+    wt, wv = bf(torch, g.standard_normal((27, cout, cin)) / math.sqrt(27 * cin))
+    b = g.standard_normal(cout).astype(np.float32)
+    btt = torch.from_numpy(b).cuda()
+    ref = O.conv3d(x, wv, b.astype(np.float64), relu=True).reshape(-1, cout)
+    yf = torch.full((n * d * h * w, cout + 24), 5.0, dtype=torch.float32, device="cuda")   # output slice [8, 8 + cout)
+    assert L.pfnn_conv3d(nn._p(bt), cin + 16, 8, nn._p(wt), cin, cout, nn._p(btt), 1, 0, None, nn._p(yf), cout + 24, 8,
+                         0, n, d, h, w, None) == 0
+    yb = torch.zeros((n * d * h * w, cout), dtype=torch.bfloat16, device="cuda")
+    assert L.pfnn_conv3d(nn._p(bt), cin + 16, 8, nn._p(wt), cin, cout, nn._p(btt), 1, 0, nn._p(yb), None, cout, 0, 0, n,
+                         d, h, w, None) == 0
+    torch.cuda.synchronize()
+    o = yf.cpu().numpy()
+    assert relerr(o[:, 8:8 + cout], ref) <= 2e-5
+    assert np.all(o[:, :8] == 5.0) and np.all(o[:, 8 + cout:] == 5.0)
+    assert relerr(yb.float().cpu().numpy(), ref) <= 8e-3
+    # backward data into a gradient that already holds values
+    dyt, dy = bf(torch, g.standard_normal((n, d, h, w, cout)))
+    wtr = torch.empty((27, cin, cout), dtype=torch.bfloat16, device="cuda")
+    assert L.pfnn_weight_transpose(nn._p(wt), nn._p(wtr), cout, cin, None) == 0
+    base = g.standard_normal((n * d * h * w, cin)).astype(np.float32)
+    dx = torch.from_numpy(base.copy()).cuda()
+    assert L.pfnn_conv3d(nn._p(dyt), cout, 0, nn._p(wtr), cout, cin, None, 0, 1, None, nn._p(dx), cin, 0, 1, n, d, h, w,
+                         None) == 0
+    torch.cuda.synchronize()
+    assert relerr(dx.cpu().numpy() - base, O.conv3d_bwd_data(dy, wv).reshape(-1, cin)) <= 2e-5
+    assert no_failed_waits(nn)
+
+
+def test_conv_halo_tile_gives_up_withheld_tile(env):
+    """The halo-tile kernel's bounded waits: its tile loads withheld, the call stores nothing, pfnn_status
+    reports PF_E_TIMEOUT once, and the next call is correct."""
+    torch, nn, O = env
+    L = nn._lib()
+    g = np.random.default_rng(12)
+    n, d, h, w, cin, cout = 1, 8, 16, 16, 16, 16
+    xt, x = bf(torch, g.standard_normal((n, d, h, w, cin)))
+    wt, wv = bf(torch, g.standard_normal((27, cout, cin)) / math.sqrt(27 * cin))
+    y = torch.full((n * d * h * w, cout), 3.0, dtype=torch.float32, device="cuda")
+    assert no_failed_waits(nn)
+    assert L.pfnn_test_withhold_stage(0, 1 << 10) == 0
+    assert L.pfnn_conv3d(nn._p(xt), cin, 0, nn._p(wt), cin, cout, None, 0, 0, None, nn._p(y), cout, 0, 0, n, d, h, w,
+                         None) == 0
+    torch.cuda.synchronize()
+    flag = nn.C.c_int(0)
+    assert L.pfnn_status(nn.C.byref(flag)) == -7 and flag.value == 1
+    assert bool(torch.all(y == 3.0))
+    assert no_failed_waits(nn)
+    assert L.pfnn_conv3d(nn._p(xt), cin, 0, nn._p(wt), cin, cout, None, 0, 0, None, nn._p(y), cout, 0, 0, n, d, h, w,
+                         None) == 0
+    torch.cuda.synchronize()
+    assert relerr(y.cpu().numpy(), O.conv3d(x, wv).reshape(-1, cout)) <= 2e-5
+    assert no_failed_waits(nn)
+
+
 def test_conv_rejects_unsupported(env):
     """Sizes the tensor-core tiles do not take are refused on the host, before any launch."""
     torch, nn, O = env

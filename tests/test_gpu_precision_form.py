@@ -113,6 +113,9 @@ def test_fp32_form_freeze_thaw_against_oracle(env):
     assert 0.0 < u_ref["uwc"] < 1.0 and u_ref["n_ice"] > 100
     assert dphi <= 1e-3
     assert duwc <= 5e-3
+    # the increments over the binary32 copy of the state keep the error estimate's rounding noise below
+    # the tolerance: about as many attempts as binary64 (stage values rounded separately took 6x more)
+    assert s32["n_accepted"] + s32["n_rejected"] <= 1.3 * (ref["n_accepted"] + ref["n_rejected"])
 
 
 # The 512^3 lognormal freeze-then-thaw workload's error study: its 128^3 crop at the top centre of the
@@ -171,6 +174,7 @@ def test_lognormal_crop_freeze_thaw_both_forms(env, lognormal_crop):
             else:
                 assert dphi <= 1e-3
                 assert duwc <= 5e-3
+                assert s["n_accepted"] + s["n_rejected"] <= 1.3 * (ref["n_accepted"] + ref["n_rejected"])
         g.close()
     print("\n" + "\n".join(report))
 

@@ -74,9 +74,11 @@ def test_slabs_equal_single_domain_full_model(env, prec, nslabs, planes):
     assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2])
     assert got[3] == ref[3] and got[4] == ref[4]
     assert (got[5]["n_ice"], got[5]["n_water"]) == (ref[5]["n_ice"], ref[5]["n_water"])
-    # halo traffic: every cut, both directions, two fields, five exchanges per attempt (replays included)
+    # halo traffic: every cut, both directions, two fields, per attempt four exchanges of stage inputs and
+    # one of the state (replays included); the binary32 form adds the binary32 copy of the state
     esz = 4 if prec == I.PREC_FP32 else 8
-    per_attempt = (nslabs - 1) * 2 * 2 * shape[0] * shape[1] * (4 * esz + 8)
+    nx = 5 if prec == I.PREC_FP32 else 4
+    per_attempt = (nslabs - 1) * 2 * 2 * shape[0] * shape[1] * (nx * esz + 8)
     assert got[6] > 0 and got[6] % per_attempt == 0
 
 
