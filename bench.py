@@ -606,6 +606,13 @@ def run_conv(args, rank, world):
                          "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                          "frac": out[top]["tflops"] / peaks["bf16_tflops"], "peak_source": kind, "traffic": None},
             "layers": out, "clocks": clk.summary()}
+    # the narrow layer is bound by memory traffic, not by the tensor cores: its input and output bytes
+    # against the copy bandwidth
+    nl = out.get("infer_l0_256")
+    if nl:
+        line["roofline_narrow"] = {"bound": "hbm", "kernel": nl["kernel"], "layer": "infer_l0_256",
+                                   "achieved": nl["io_gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                   "frac": nl["frac_of_hbm"], "peak_source": kind, "traffic": None}
     print(json.dumps(line), flush=True)
 
 

@@ -27,6 +27,8 @@ extern "C" {
 #endif
 
 /* Forward (flip = 0): y[v][co] = act(bias[co] + sum_{t,ci} x[v + off(t)][ci] w[t][co][ci]).
+ * (16 or 32 channels in and out on grids of at least 8 x 16 x 4 cells: one shared-memory tile per
+ * 8 x 16 x 4 brick, the three taps along z of each lateral offset in one MMA; else one TMA box per tap.)
  * Backward data (flip = 1, w = transposed weights [27][Cin][Cout], cin/cout swapped):
  *   dx[v][ci] = sum_{t,co} dy[v - off(t)][co] w[t][co][ci].
  * cin a multiple of 16; cout a multiple of 16 up to 256; act = ReLU when relu != 0.  ldx, xoff, ldy and
@@ -46,7 +48,9 @@ pf_status pfnn_status(int* failed);
  * loads of pipeline stage `stage` (0 <= stage < 27 * cin / ck) and bounds every pipeline wait by `tries`
  * (1 <= tries <= 2^24) instead of 2^24.  The waits for that stage then give up: the call finishes
  * without storing its output, TMEM freed after every issued MMA has retired, and pfnn_status reports
- * it.  The setting applies to one call only.  Nothing faults: the withheld stage is an empty wait. */
+ * it.  The setting applies to one call only.  Nothing faults: the withheld stage is an empty wait.
+ * Layers of 16 or 32 channels in and out on grids of at least 8 x 16 x 4 (W x H x D) run the halo-tile
+ * kernel, which loads one tile per block: there any stage >= 0 withholds that tile. */
 pf_status pfnn_test_withhold_stage(int stage, long long tries);
 
 /* Weight gradient: dw[t][co][ci] += sum_v dy[v][co] x[v + off(t)][ci], on the fifth-generation tensor cores:

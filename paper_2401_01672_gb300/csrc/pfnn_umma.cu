@@ -300,14 +300,19 @@ k_conv_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 // For 16 or 32 channels the per-tap boxes of k_conv_umma are 32- or 64-byte rows and the 27 boxes of a
 // 128-voxel tile move 27 times its input through TMA.  Here a block loads the input of its whole brick
 // (8 x 16 x DZ cells, x fastest) once, with a one-cell halo: a (DZ + 2) x 18 x 10 tile per 8-channel
-// chunk, unswizzled, so that every cell is a 16-byte row and a row of 10 cells is 160 contiguous bytes.  The A
-// operand of one tap is then a window of that tile: for output plane zo and tap (dz, dy, dx), the 128 rows
-// (8 x by 16 y) start at cell (dx + 1, dy + 1, zo + dz + 1) of the tile; 8 consecutive x cells are one
-// 8 x 16-byte core matrix, consecutive y rows are 160 bytes apart (the stride between core matrices along
-// M) and consecutive 8-channel chunks one chunk apart (the stride along K).  The descriptor start is a
-// multiple of 16 bytes, as the unswizzled layout requires.  The weights of all 27 taps stay in shared
-// memory in the same core-matrix layout: [tap][chunk][cout][8 channels].  Per brick: DZ x 27 x cin/16 MMAs
-// (M = 128, N = cout, K = 16) into DZ accumulators of cout columns each.
+// chunk, unswizzled, so that every cell is a 16-byte row and a row of 10 cells is 160 contiguous bytes.
+// The A operand is a window of that tile: for tile plane z' and lateral offset (dy, dx), the 128 rows
+// (8 x by 16 y) start at cell (dx + 1, dy + 1, z'); 8 consecutive x cells are one 8 x 16-byte core
+// matrix, consecutive y rows are 160 bytes apart (the stride between core matrices along M) and
+// consecutive 8-channel chunks one chunk apart (the stride along K); the start is a multiple of 16 bytes,
+// as the unswizzled layout requires.  One window serves the three taps (dz = -1, 0, +1) of its (dy, dx):
+// tile plane z' feeds output planes o = z' - 1 - dz.  The B operand stacks the three taps' weights along
+// N (3 cout rows: dz = -1, 0, +1), and the accumulators of the output planes lie in TMEM at decreasing
+// columns, plane o at (DZ + 1 - o) cout, so the three column groups of one MMA are the accumulators of
+// planes z', z' - 1 and z' - 2 (planes -2, -1, DZ and DZ + 1 are scratch).  Per brick: (DZ + 2) x 9 x
+// cin/16 MMAs of M = 128, N = 3 cout, K = 16 (a third of the A reads from shared memory of one MMA per
+// tap); the accumulators start from zero written by tcgen05.st.  The weights of all taps stay in shared
+// memory as [dy, dx][chunk][dz, cout][8 channels]; backward data (flipped taps) copies tap 26 - t there.
 struct HaloArgs {
     int cin, cout, dz_planes;     // channels in/out, output planes per brick
     int D, H, W;                  // grid of one sample
@@ -353,32 +358,30 @@ __device__ __forceinline__ void umma_f16_w(uint32_t tmem_d, uint32_t alo, uint32
 
 // The MMAs of one brick.  a_lo / b_lo: low descriptor words of the tile and weight bases; the start field
 // (bits 0-13, 16-byte units) is advanced by adding to the low word (the shared window lies below 256 KB,
-// so it never carries out).  Tap t = 9 (dz + 1) + 3 (dy + 1) + (dx + 1) reads the window at tile cell
-// (dx + 1, dy + 1, zo + dz + 1); flipped taps (backward data) read the window of tap 26 - t.
-template <bool FLIP, int NKB>
+// so it never carries out).
+template <int NKB>
 __device__ __forceinline__ void halo_issue(uint32_t tmem, uint32_t a_lo, uint32_t a_hi, uint32_t b_lo, uint32_t b_hi,
                                            uint32_t idesc, int planes, int cout, uint32_t chunk16) {
+    for (int zt = 0; zt < planes + 2; ++zt) {
+        const uint32_t d = tmem + (uint32_t)((planes + 1 - zt) * cout);  // accumulator of output plane zt
+        const uint32_t a_z = a_lo + (uint32_t)(zt * HT_Y * HT_X);
 #pragma unroll
-    for (int t = 0; t < 27; ++t) {
-        const int u = FLIP ? 26 - t : t;
-        const uint32_t off = (uint32_t)(((u / 9) * HT_Y + (u / 3) % 3) * HT_X + u % 3);
+        for (int l = 0; l < 9; ++l) {  // l = 3 (dy + 1) + (dx + 1)
+            const uint32_t off = (uint32_t)((l / 3) * HT_X + l % 3);
 #pragma unroll
-        for (int kb = 0; kb < NKB; ++kb) {
-            const uint32_t a_t = a_lo + off + (uint32_t)(2 * kb) * chunk16;
-            const uint32_t b_t = b_lo + (uint32_t)((t * 2 * NKB + 2 * kb) * cout);
-            const uint32_t accf = (t > 0 || kb > 0) ? 1u : 0u;
-            // output plane zo: its accumulator, the window one tile plane further
-            for (int zo = 0; zo < planes; ++zo)
-                umma_f16_w(tmem + (uint32_t)(zo * cout), a_t + (uint32_t)(zo * HT_Y * HT_X), a_hi, b_t, b_hi, idesc,
-                           accf);
+            for (int kb = 0; kb < NKB; ++kb)
+                umma_f16_w(d, a_z + off + (uint32_t)(2 * kb) * chunk16, a_hi,
+                           b_lo + (uint32_t)((l * 2 * NKB + 2 * kb) * 3 * cout), b_hi, idesc, 1u);
         }
     }
 }
 
-// Weights of all taps into shared memory as [tap][chunk][cout][8], in rounds of 7 16-byte vectors per
-// thread: each round loads all of its vectors (read-only path) before storing them, so the copy costs one
-// round trip to L2 per 14 KB (one for 16 x 16 channels, four for 32 x 32).
-__device__ __forceinline__ void halo_weights(const bf16* __restrict__ w, unsigned char* dst, int cout, int nkc) {
+// Weights of all taps into shared memory as [dy, dx][chunk][dz, cout][8] (tap t = 9 (dz + 1) + l,
+// l = 3 (dy + 1) + (dx + 1); flipped: the tap 26 - t), in rounds of 7 16-byte vectors per thread: each
+// round loads all of its vectors (read-only path) before storing them, so the copy costs one round trip
+// to L2 per 14 KB (one for 16 x 16 channels, four for 32 x 32).
+__device__ __forceinline__ void halo_weights(const bf16* __restrict__ w, unsigned char* dst, int cout, int nkc,
+                                             int flip) {
     constexpr int CAP = 7;
     const int nvec = 27 * cout * nkc;
     const uint4* src = reinterpret_cast<const uint4*>(w);
@@ -395,11 +398,24 @@ __device__ __forceinline__ void halo_weights(const bf16* __restrict__ w, unsigne
             if (q < nvec) {
                 const int kc = q % nkc;
                 const int co = (q / nkc) % cout;
-                const int t = q / (nkc * cout);
-                *reinterpret_cast<uint4*>(dst + ((size_t)(t * nkc + kc) * cout + co) * 16) = v[j];
+                int t = q / (nkc * cout);
+                if (flip) t = 26 - t;
+                const int dzi = t / 9, l = t % 9;
+                *reinterpret_cast<uint4*>(dst + ((size_t)(l * nkc + kc) * 3 * cout + dzi * cout + co) * 16) = v[j];
             }
         }
     }
+}
+
+// zero the accumulator columns [0, cols) of this warp's TMEM lane quadrant
+__device__ __forceinline__ void tmem_zero(uint32_t taddr, int cols) {
+    const uint32_t z = 0u;
+    for (int c = 0; c < cols; c += 16)
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+            "%1, %1};" ::"r"(taddr + (uint32_t)c), "r"(z)
+            : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // One block per brick: thread 0 issues the tile's TMA loads (one box per 8-channel chunk, zero fill
@@ -447,8 +463,12 @@ k_conv_halo(const __grid_constant__ CUtensorMap tmX, const HaloArgs p) {
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    halo_weights(p.w, sm + p.tile_bytes, p.cout, nkc);
+    halo_weights(p.w, sm + p.tile_bytes, p.cout, nkc, p.flip);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // the TMEM address is in shared memory
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tmem_zero(*tmem_slot + ((uint32_t)(warp * 32) << 16), (p.dz_planes + 4) * p.cout);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -459,16 +479,11 @@ k_conv_halo(const __grid_constant__ CUtensorMap tmX, const HaloArgs p) {
         if (ok) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint64_t da = desc_plain(tile0, p.chunk_bytes, HT_ROW);
-            const uint64_t db = desc_plain(w0, (uint32_t)p.cout * 16u, 128u);
+            const uint64_t db = desc_plain(w0, 3u * (uint32_t)p.cout * 16u, 128u);
             const uint32_t alo = (uint32_t)da, ahi = (uint32_t)(da >> 32), blo = (uint32_t)db, bhi = (uint32_t)(db >> 32);
             const uint32_t c16 = p.chunk_bytes >> 4;
-            if (p.flip) {
-                if (nkc == 2) halo_issue<true, 1>(tmem, alo, ahi, blo, bhi, p.idesc, p.dz_planes, p.cout, c16);
-                else halo_issue<true, 2>(tmem, alo, ahi, blo, bhi, p.idesc, p.dz_planes, p.cout, c16);
-            } else {
-                if (nkc == 2) halo_issue<false, 1>(tmem, alo, ahi, blo, bhi, p.idesc, p.dz_planes, p.cout, c16);
-                else halo_issue<false, 2>(tmem, alo, ahi, blo, bhi, p.idesc, p.dz_planes, p.cout, c16);
-            }
+            if (nkc == 2) halo_issue<1>(tmem, alo, ahi, blo, bhi, p.idesc, p.dz_planes, p.cout, c16);
+            else halo_issue<2>(tmem, alo, ahi, blo, bhi, p.idesc, p.dz_planes, p.cout, c16);
         } else {
             s_fail = 1;
         }
@@ -491,7 +506,7 @@ k_conv_halo(const __grid_constant__ CUtensorMap tmX, const HaloArgs p) {
             const bool inside = inxy && z < p.D;
             const long long v = (((long long)bn * p.D + z) * p.H + y) * p.W + x;
             float o[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(zo * p.cout + c0), o);  // whole warp
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((p.dz_planes + 1 - zo) * p.cout + c0), o);
             if (!inside) continue;
 #pragma unroll
             for (int q = 0; q < 16; ++q) o[q] += bias[q];
@@ -738,10 +753,10 @@ pf_status conv_halo(const void* x, int ldx, int xoff, const void* w, int cin, in
     g_test_withhold = -1;
     g_test_tries = 0;
     a.w_bytes = (unsigned)(27 * cout * cin * 2);
-    // 8 output planes per brick where the tile and the weights leave room for two blocks per SM, else 4
-    int dzp = 8;
+    // 4 output planes per brick: 16 -> 16 channels then fit four blocks per SM (48.6 KB of shared memory,
+    // 8 x 16 TMEM columns each), the wider layers two (32 x 32: one)
+    const int dzp = 4;
     auto chunk = [](int dz) { return round1024((unsigned)(HT_ROW * HT_Y * (dz + 2))); };
-    if ((size_t)(cin / 8) * chunk(8) + a.w_bytes > 110u * 1024u) dzp = 4;
     a.dz_planes = dzp;
     a.chunk_bytes = chunk(dzp);
     a.tile_bytes = (unsigned)(cin / 8) * a.chunk_bytes;
@@ -749,8 +764,9 @@ pf_status conv_halo(const void* x, int ldx, int xoff, const void* w, int cin, in
     a.tx = (wd + HB_X - 1) / HB_X;
     a.ty = (h + HB_Y - 1) / HB_Y;
     a.tz = (d + dzp - 1) / dzp;
-    a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(cout >> 3) << 17) | ((unsigned)(UM >> 4) << 24);
-    const int cols = dzp * cout;
+    // MMA N = 3 cout: the taps dz = -1, 0, +1 of one lateral offset
+    a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(3 * cout >> 3) << 17) | ((unsigned)(UM >> 4) << 24);
+    const int cols = (dzp + 4) * cout;
     a.tmem_cols = cols <= 32 ? 32 : (cols <= 64 ? 64 : (cols <= 128 ? 128 : 256));
     a.bias = bias;
     a.w = (const bf16*)w;
