@@ -60,7 +60,7 @@ FLOPS_COMB = [4, 6, 8, 12, 24]
 # coefficients (64 B where the Allen-Cahn arithmetic runs, 24 B in the bulk), read instead of
 # recomputed on the binary64 pipe that bounds it.  Binary32 form (increments over a binary32 copy of the
 # state): 531.3 MB, the method's 76 B.
-TRAFFIC_F64_S5_PER_CELL = 144.2
+TRAFFIC_F64_S5_PER_CELL = None   # 144.2 before the coupling moved onto the compacted slots; recapture
 TRAFFIC_F32_S5_PER_CELL = 75.1
 KERNEL_BYTES_F64_S5 = None
 

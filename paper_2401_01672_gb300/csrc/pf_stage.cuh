@@ -172,6 +172,10 @@ __device__ __forceinline__ bool uniform_01(float c, float a0, float a1, float a2
     return r;
 }
 __device__ __forceinline__ bool is_one(double v) { return __double_as_longlong(v) == 0x3FF0000000000000LL; }
+__device__ __forceinline__ bool is_01(double v) {
+    const long long b = __double_as_longlong(v);
+    return b == 0LL || b == 0x3FF0000000000000LL;
+}
 __device__ __forceinline__ bool is_one(float v) { return __float_as_int(v) == 0x3F800000; }
 
 template <typename T>
@@ -510,7 +514,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
     constexpr bool COMPACT = !F32 && !TEMP && BY <= 8;
     __shared__ int s_wcnt[BY];
     __shared__ int s_slot_xy[COMPACT ? TX * BY : 1];
-    __shared__ T s_slot[COMPACT ? 4 : 1][COMPACT ? TX * BY : 1];
+    // per slot: phi's z neighbours, theta, W; full model also the heat flux divergence and the cell's
+    // coefficients of rho c and rho L, so the latent coupling runs on the slots too
+    constexpr int NSLOT = COMPACT ? (STATIC ? 10 : 4) : 1;
+    __shared__ T s_slot[NSLOT][COMPACT ? TX * BY : 1];
 
     // Dirichlet faces of this column (x and y faces are fixed along the march)
     const int dmask = a.cf.dirichlet;
@@ -635,11 +642,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
                 if constexpr (HAS_PH) ua_p = a.ua_ph[id];
             }
             if constexpr (STATIC) {
-                // a bulk cell needs only 1/(rho c) at its phi; stage 1 also counts the pore cells (W)
+                // a cell whose dphi is exactly 0 with phi exactly 0 or 1 (bulk, or no water) needs only
+                // 1/(rho c) at its phi; stage 1 also counts the pore cells (W)
                 if (STAGE == 1 || !bulk) sW = St_W[id];
-                if (bulk) {
-                    sIR = St_I[(is_one(phc) ? NC : 0) + id];
-                } else {
+                if (bulk || is_01(phc)) sIR = St_I[(is_one(phc) ? NC : 0) + id];
+                if (!bulk) {
                     sC0 = St_C[id]; sC1 = St_C[NC + id]; sC2 = St_C[2 * NC + id];
                     sD0 = St_D[id]; sD1 = St_D[NC + id];
                 }
@@ -697,19 +704,22 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
         }
         // ---- Allen-Cahn rate (eq. Allen-Cahn-equation): dphi = W (klap lap + f/2), W = 2 I_W/(alpha xi^2)
         T dph = T(0);
+        bool need = false;  // the Allen-Cahn arithmetic runs (W > 0, not bulk)
+        T dth_slot = T(0);  // full model, compacted: the latent coupling's result from the slot
         if constexpr (!TEMP) {
             T W = T(0);
             if (inside && !bulk) {  // bulk cells: dphi = 0 without arithmetic
                 if constexpr (STATIC) W = sW;
                 else W = FMA(K.wb, Gc, K.wa);
             }
-            const bool need = positive(W);
+            need = positive(W);
             if constexpr (COMPACT) {
                 // Binary64: the cells of the block that need the Allen-Cahn arithmetic are packed into
                 // consecutive slots (warp ballots and a prefix over the block's warps), so each warp runs
                 // it on full lanes; a row of 32 cells mixing glass, bulk and interface cells would run it
                 // on all lanes.  Owners leave their z neighbours, theta and W in the slot; the lateral
-                // neighbours are read from the plane in shared memory.
+                // neighbours are read from the plane in shared memory.  (Ordering the slots so that the
+                // cells taking the Sigma limiter come first was measured: no gain.)
                 const unsigned m = __ballot_sync(0xffffffffu, need);
                 if (tx == 0) s_wcnt[ty] = __popc(m);
                 __syncthreads();
@@ -727,18 +737,35 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
                     s_slot[1][slot] = php;
                     s_slot[2][slot] = thc;
                     s_slot[3][slot] = W;
+                    if constexpr (STATIC) {
+                        s_slot[4][slot] = div;
+                        s_slot[5][slot] = sC0;
+                        s_slot[6][slot] = sC1;
+                        s_slot[7][slot] = sC2;
+                        s_slot[8][slot] = sD0;
+                        s_slot[9][slot] = sD1;
+                    }
                 }
                 __syncthreads();
                 for (int q = tid; q < total; q += TX * BY) {
                     const int xy = s_slot_xy[q];
                     const int qx = xy & 255, qy = xy >> 8;
-                    // the rate goes back into the slot's first entry (read above by this thread only)
-                    s_slot[0][q] = ac_rate(s_ph[b][qy + 1][qx + 1], s_ph[b][qy + 1][qx], s_ph[b][qy + 1][qx + 2],
-                                           s_ph[b][qy][qx + 1], s_ph[b][qy + 2][qx + 1], s_slot[0][q], s_slot[1][q],
-                                           s_slot[2][q], s_slot[3][q]);
+                    const T pc = s_ph[b][qy + 1][qx + 1];
+                    const T r = ac_rate(pc, s_ph[b][qy + 1][qx], s_ph[b][qy + 1][qx + 2], s_ph[b][qy][qx + 1],
+                                        s_ph[b][qy + 2][qx + 1], s_slot[0][q], s_slot[1][q], s_slot[2][q], s_slot[3][q]);
+                    // the rate goes back into the slot's first entry, the coupling's result into the second
+                    // (both read above by this thread only)
+                    if constexpr (STATIC) {
+                        const T rhoc = FMA(pc, FMA(pc, s_slot[7][q], s_slot[6][q]), s_slot[5][q]);
+                        s_slot[1][q] = FMA(FMA(pc, s_slot[9][q], s_slot[8][q]), r, s_slot[4][q]) * recip_pos(rhoc);
+                    }
+                    s_slot[0][q] = r;
                 }
                 __syncthreads();
-                if (need) dph = s_slot[0][slot];
+                if (need) {
+                    dph = s_slot[0][slot];
+                    if constexpr (STATIC) dth_slot = s_slot[1][slot];
+                }
             } else if (need) {
                 T q_xm = T(0), q_xp = T(0), q_ym = T(0), q_yp = T(0);
                 if constexpr (F32) {
@@ -758,8 +785,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
             // ---- latent-heat coupling
             T dth = T(0);
             if constexpr (STATIC) {
-                if (bulk) {
-                    dth = div * sIR;  // dphi = 0
+                if (COMPACT && need) {
+                    dth = dth_slot;
+                } else if (!need && (bulk || is_01(phc))) {
+                    dth = div * sIR;  // dphi = 0 and phi exactly 0 or 1
                 } else {
                     const T rhoc = FMA(phc, FMA(phc, sC2, sC1), sC0);
                     dth = FMA(FMA(phc, sD1, sD0), dph, div) * recip_pos(rhoc);
