@@ -426,7 +426,8 @@ MACRO_CASES = {
 
 def run_macro(args, rank, world):
     """The paper's macro-scale parametric study (Sec. 3.1-3.2) on the vessel at N3 cells: 5 h cooling
-    through the cap at -25 K, 5 h heating at +20 K, binary64, tol 1e-6.  Reports each run's wall time
+    through the cap at -25 K, 5 h heating at +20 K, binary64 (or the binary32-field form with --form f32),
+    tol 1e-6.  Reports each run's wall time
     next to the paper's Table 3 (its CPU cluster; context) and the qualitative findings the paper
     states about the ice-fraction curves.  Rank 0 only (one run = one GPU)."""
     if rank != 0:
@@ -438,7 +439,8 @@ def run_macro(args, rank, world):
         for nm in names:
             model, rx, sigma, gamma = MACRO_CASES[nm]
             w = I.macro_case(args.macro_n3, model, rx, sigma=sigma, gamma=gamma)
-            runs[nm] = macro.run_case(w, max_attempts=args.macro_cap)
+            runs[nm] = macro.run_case(w, max_attempts=args.macro_cap,
+                                      precision=I.PREC_FP32 if args.form == "f32" else I.PREC_FP64)
             print(json.dumps({"case": nm, "status": runs[nm]["status"], "wall_s": runs[nm]["wall_s"],
                               "attempts": runs[nm]["attempts"]}), file=sys.stderr, flush=True)
     # water above the bead bed, as a share of all water: the ice fraction at which a front coming down
@@ -491,7 +493,8 @@ def run_macro(args, rank, world):
     headline = "sigmap1p_small" if "sigmap1p_small" in runs else names[0]
     line = {"metric": "macro freeze-thaw run wall time (10 h physical)", "value": runs[headline]["wall_s"],
             "unit": "s", "higher_is_better": False, "n_gpus": 1, "steps": runs[headline]["attempts"], "warmup": 0,
-            "dtype": "f64", "data": "synthetic", "scaling": "weak",
+            "dtype": "f32 fields / f64 state" if args.form == "f32" else "f64", "data": "synthetic",
+            "scaling": "weak",
             "config": {"workload": f"macro_vessel_n3_{args.macro_n3}", "grid": list(w0.shape), "h_m": w0.h,
                        "beads": w0.extra["n_spheres"], "bed_top_m": w0.extra["bed_top"], "tol": 1e-6,
                        "headline_case": headline},
@@ -729,7 +732,7 @@ def main():
     ap.add_argument("--no-crop-study", action="store_true", help="full512: skip the 128^3 crop error study")
     ap.add_argument("--no-cycle", action="store_true",
                     help="full512: skip the whole-grid freeze-then-thaw cycle of both forms (time to solution)")
-    ap.add_argument("--form", default="f64", choices=["f64", "f32"], help="stages: precision form")
+    ap.add_argument("--form", default="f64", choices=["f64", "f32"], help="stages, macro: precision form")
     ap.add_argument("--max-steps", type=int, default=600, help="sweep48, uwc: attempt cap per instance")
     ap.add_argument("--macro-n3", type=int, default=100, help="macro: cells along the vessel height (100/200/400)")
     ap.add_argument("--macro-cap", type=int, default=1_500_000, help="macro: attempt cap per run")
