@@ -41,6 +41,28 @@ def test_macro_vessel_cooling(env, model, rx, sigma):
     assert min(p["theta_min"] for p in r["curve"]) >= -25.0 - 1e-6
 
 
+def test_macro_vessel_binary32_form_follows_binary64(env):
+    """The vessel (N3 = 40, SigmaP1-P, small sigma, first 40 minutes of cooling) in the binary32-field
+    form: its stage inputs are increments over a binary32 copy of the state, so the error estimate keeps
+    no rounding floor above the tolerance and it takes at most twice the binary64 attempts (binary32
+    stage values took several times more); the sampled ice fractions agree to 1e-3."""
+    macro = env
+    out = {}
+    for prec in (I.PREC_FP64, I.PREC_FP32):
+        w = I.macro_case(40, I.MODEL_FULL, I.REACT_SIGMAP1P, sigma="small")
+        w.extra["t_end"] = 2400.0
+        out[prec] = macro.run_case(w, n_samples=12, max_attempts=400000, precision=prec)
+    r64, r32 = out[I.PREC_FP64], out[I.PREC_FP32]
+    assert r64["status"] == "ok" and r32["status"] == "ok"
+    i64 = np.array([p["ice_fraction"] for p in r64["curve"]])
+    i32 = np.array([p["ice_fraction"] for p in r32["curve"]])
+    print(f"\nbinary64 {r64['attempts']} attempts, binary32 form {r32['attempts']}, "
+          f"max |d ice fraction| {np.max(np.abs(i64 - i32)):.2e}")
+    assert i64[-1] > 0.0
+    assert np.max(np.abs(i64 - i32)) <= 1e-3
+    assert r32["attempts"] <= 2 * r64["attempts"]
+
+
 def test_uwc_falls_with_supercooling_coarse(env):
     """Micro-scale vessel (bead radius 5 um) on a coarse mesh: at the larger supercooling the ice
     reaches into smaller pores (Gibbs-Thomson), so less water stays unfrozen in the bed."""
