@@ -183,7 +183,7 @@ class OracleCrop:
     def describe(self, n, el, threads):
         c = self.SHAPE
         return (f"{n} Merson steps on a {c[0]}x{c[1]}x{c[2]} crop (top of the {self.full}^3 workload, "
-                f"{self.n_beads} nearby beads), {threads} thread{'s' if threads > 1 else ''}, {el:.1f} s")
+                f"{self.n_beads} nearby beads), {threads} thread{'s' if threads > 1 else ''}, {el:.3g} s")
 
 
 def _time_oracle(oc, seconds, min_steps):
