@@ -48,8 +48,9 @@ TOL = 1e-6
 # each once per cell.  Binary64 path, bytes per cell for stages 1..5:
 BYTES_F64 = [56, 72, 88, 104, 104]          # sum 424 = 84.8 B per cell-stage
 # Binary32-field form (stage buffers, G and the binary32 copy y32 of the state in 4 B, state y in 8 B;
-# stage 1 reads y and writes y32, k1 and the increment d2; stages 2-5 read y32 and their increment):
-BYTES_F32 = [44, 36, 52, 52, 76]            # sum 260 = 52 B per cell-stage
+# stage 1 reads y32 and writes k1 and the increment d2; stages 2-5 read y32 and their increment; stage 5
+# reads y and writes y' and its binary32 copy):
+BYTES_F32 = [28, 36, 52, 52, 84]            # sum 252 = 50.4 B per cell-stage
 # Floating-point operations per cell (FMA = 2, division = 1) of the right-hand side as written
 # (blends 6+6+6, fluxes 24, Allen-Cahn 16, latent coupling 6) plus each stage's combination.
 FLOPS_RHS = 64
@@ -59,9 +60,9 @@ FLOPS_COMB = [4, 6, 8, 12, 24]
 # it is captured again).  Binary64: 1027.7 MB -- the method's 104 B plus the per-cell blend
 # coefficients (64 B where the Allen-Cahn arithmetic runs, 24 B in the bulk), read instead of
 # recomputed on the binary64 pipe that bounds it.  Binary32 form (increments over a binary32 copy of the
-# state): 531.3 MB, the method's 76 B.
+# state, which stage 5 writes): 585.6 MB, the method's 84 B.
 TRAFFIC_F64_S5_PER_CELL = 145.2
-TRAFFIC_F32_S5_PER_CELL = 75.1
+TRAFFIC_F32_S5_PER_CELL = 82.7
 KERNEL_BYTES_F64_S5 = None
 
 

@@ -45,7 +45,10 @@ struct pf_grid {
     void* k1_th = nullptr; void* k1_ph = nullptr;
     void* k3_th = nullptr; void* k3_ph = nullptr;
     void* k4_th = nullptr; void* k4_ph = nullptr;
-    void* y32_th = nullptr; void* y32_ph = nullptr;  // binary32 form of the full model: stage inputs are increments over it
+    // binary32 form of the full model: binary32 copies of the two state buffers (the stage inputs are
+    // increments over the current one); set with the state, written by stage 5 beside the candidate state
+    void* y32_th[2] = {nullptr, nullptr};
+    void* y32_ph[2] = {nullptr, nullptr};
     double* G64 = nullptr;
     float* G32 = nullptr;
     double* statics = nullptr;  // full model, binary64: NSTATIC per-cell coefficient arrays (see StageArgs)
@@ -78,6 +81,7 @@ static pf_status fail(pf_grid* g, pf_status s, const std::string& msg) {
 static bool is_f32(const pf_grid* g) { return g->prec == PF_PREC_FP32_FIELDS; }
 extern "C" {
 static pf_status refresh_g32(pf_grid* g);
+static pf_status refresh_y32(pf_grid* g, int b);
 }
 static size_t fbytes(const pf_grid* g) { return is_f32(g) ? sizeof(float) : sizeof(double); }
 static bool has_th(const pf_grid* g) { return g->model != PF_MODEL_MICRO; }
@@ -441,7 +445,10 @@ static StageArgs<T> make_args(pf_grid* g) {
     a.k1_th = (T*)g->k1_th; a.k1_ph = (T*)g->k1_ph;
     a.k3_th = (T*)g->k3_th; a.k3_ph = (T*)g->k3_ph;
     a.k4_th = (T*)g->k4_th; a.k4_ph = (T*)g->k4_ph;
-    a.y32_th = (T*)g->y32_th; a.y32_ph = (T*)g->y32_ph;
+    for (int b = 0; b < 2; ++b) {
+        a.y32_th[b] = (T*)g->y32_th[b];
+        a.y32_ph[b] = (T*)g->y32_ph[b];
+    }
     if constexpr (std::is_same<T, float>::value) a.G = g->G32;
     else a.G = g->G64;
     a.zc = g->zc;
@@ -606,8 +613,10 @@ static pf_status create_impl(int n1, int n2, int n3, double h, int model, int re
         g->ua_ph = AG(fbytes(g)); g->ub_ph = AG(fbytes(g)); g->k1_ph = A(nf); g->k3_ph = A(nf); g->k4_ph = A(nf);
     }
     if (is_f32(g) && model == PF_MODEL_FULL) {
-        g->y32_th = AG(4);
-        g->y32_ph = AG(4);
+        for (int b = 0; b < 2; ++b) {
+            g->y32_th[b] = AG(4);
+            g->y32_ph[b] = AG(4);
+        }
     }
     g->G64 = (double*)AG(8);
     if (is_f32(g)) g->G32 = (float*)AG(4);
@@ -652,6 +661,10 @@ static pf_status create_impl(int n1, int n2, int n3, double h, int model, int re
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
         if (g->y_th[b]) e = cudaMemsetAsync((char*)g->y_th[b] - gbytes, 0, 8 * (size_t)g->NA, g->stream);
         if (e == cudaSuccess && g->y_ph[b]) e = cudaMemsetAsync((char*)g->y_ph[b] - gbytes, 0, 8 * (size_t)g->NA, g->stream);
+        if (e == cudaSuccess && g->y32_th[b])
+            e = cudaMemsetAsync((char*)g->y32_th[b] - gbytes / 2, 0, 4 * (size_t)g->NA, g->stream);
+        if (e == cudaSuccess && g->y32_ph[b])
+            e = cudaMemsetAsync((char*)g->y32_ph[b] - gbytes / 2, 0, 4 * (size_t)g->NA, g->stream);
     }
     if (e != cudaSuccess) {
         destroy_impl(g);
@@ -695,6 +708,18 @@ static pf_status refresh_g32(pf_grid* g) {
     if (!g->G32) return PF_OK;
     k_to_f32<<<blocks_for(g->NA, 256), 256, 0, g->stream>>>(g->G64 - go, g->G32 - go, g->NA);
     count_launch();
+    PF_CUDA(g, cudaGetLastError());
+    return PF_OK;
+}
+
+// Binary32 copy of state buffer b (binary32 form of the full model), every allocated cell (ghost planes
+// included), rounded to nearest like the stage kernels' conversion.
+static pf_status refresh_y32(pf_grid* g, int b) {
+    if (!has_y32(g)) return PF_OK;
+    const long long go = (long long)g->zg_lo * g->n1 * g->n2;
+    k_to_f32<<<blocks_for(g->NA, 256), 256, 0, g->stream>>>(g->y_th[b] - go, (float*)g->y32_th[b] - go, g->NA);
+    k_to_f32<<<blocks_for(g->NA, 256), 256, 0, g->stream>>>(g->y_ph[b] - go, (float*)g->y32_ph[b] - go, g->NA);
+    count_launch(2);
     PF_CUDA(g, cudaGetLastError());
     return PF_OK;
 }
@@ -784,6 +809,8 @@ pf_status pf_set_state(pf_grid* g, const double* theta, const double* phi, doubl
     c->equilibrium = 0;
     c->eq_window = 0.0;
     pf_status s = push_ctrl(g);
+    if (s != PF_OK) return s;
+    s = refresh_y32(g, 0);
     if (s != PF_OK) return s;
     PF_CUDA(g, cudaStreamSynchronize(g->stream));
     return PF_OK;
@@ -1530,23 +1557,23 @@ long long pf_batch_iterations(const pf_batch* b) { return b ? b->iters : -1; }
 // error maximum and the pore counts accumulate over all slabs and one controller decides).
 
 namespace {
-// Pointers (local plane 0) of one slab's exchanged buffers: [theta, phi][y0, y1, ua, ub, y32].
+// Pointers (local plane 0) of one slab's exchanged buffers: [theta, phi][y0, y1, ua, ub, y32_0, y32_1].
 struct SlabTab {
-    void* f[2][5];
+    void* f[2][6];
     int n3;
     int pad;
 };
 
 // which: 0 = ua, 1 = ub (stage inputs written by the stage just run), 2 = y[cur ^ 1] (the step's
-// candidate state), 3 = y[cur] (the state), 4 = y32 (the binary32 copy of the state stage 1 writes in
-// the binary32 form of the full model).  blockIdx.y = cut * 4 + direction * 2 + field.
+// candidate state), 3 = y[cur] (the state), 4 = y32[cur ^ 1] (the binary32 copy of the candidate state
+// that stage 5 writes in the binary32 form of the full model).  blockIdx.y = cut * 4 + direction * 2 + field.
 template <typename TF>
 __global__ void k_halo(const SlabTab* __restrict__ tab, long long plane, int which, int fields,
                        const Ctrl* __restrict__ c) {
     const int r = blockIdx.y;
     const int cut = r >> 2, dir = (r >> 1) & 1, f = r & 1;
     if (!((fields >> f) & 1)) return;
-    const int slot = which < 2 ? 2 + which : (which == 2 ? (c->cur ^ 1) : (which == 3 ? c->cur : 4));
+    const int slot = which < 2 ? 2 + which : (which == 2 ? (c->cur ^ 1) : (which == 3 ? c->cur : 4 + (c->cur ^ 1)));
     const SlabTab& lo = tab[cut];
     const SlabTab& hi = tab[cut + 1];
     const TF* src;
@@ -1618,7 +1645,7 @@ static cudaError_t slabs_enqueue_attempt(pf_slabs* S, cudaStream_t st) {
             if (e != cudaSuccess) return e;
         }
         cudaError_t e = halo(S, stage == 5 ? 2 : (stage % 2 == 1 ? 0 : 1), st);
-        if (e == cudaSuccess && stage == 1 && has_y32(S->s[0])) e = halo(S, 4, st);
+        if (e == cudaSuccess && stage == 5 && has_y32(S->s[0])) e = halo(S, 4, st);
         if (e != cudaSuccess) return e;
     }
     k_controller<<<1, 32, 0, st>>>(S->s[0]->dctrl);
@@ -1709,7 +1736,8 @@ pf_status pf_slabs_create(int n1, int n2, int n3, double h, int model, int react
         SlabTab& t = tab[q];
         t.f[0][0] = g->y_th[0]; t.f[0][1] = g->y_th[1]; t.f[0][2] = g->ua_th; t.f[0][3] = g->ub_th;
         t.f[1][0] = g->y_ph[0]; t.f[1][1] = g->y_ph[1]; t.f[1][2] = g->ua_ph; t.f[1][3] = g->ub_ph;
-        t.f[0][4] = g->y32_th; t.f[1][4] = g->y32_ph;
+        t.f[0][4] = g->y32_th[0]; t.f[0][5] = g->y32_th[1];
+        t.f[1][4] = g->y32_ph[0]; t.f[1][5] = g->y32_ph[1];
         t.n3 = g->n3;
         t.pad = 0;
     }
@@ -1772,6 +1800,11 @@ pf_status pf_slabs_set_state(pf_slabs* S, const double* theta, const double* phi
         }
     }
     PF_SCUDA(S, halo(S, 3, g0->stream));
+    // the binary32 copies again, now that the ghost planes of the state are filled
+    for (pf_grid* g : S->s) {
+        pf_status st = refresh_y32(g, 0);
+        if (st != PF_OK) return sfail(S, st, g->err);
+    }
     PF_SCUDA(S, cudaStreamSynchronize(g0->stream));
     return PF_OK;
 }

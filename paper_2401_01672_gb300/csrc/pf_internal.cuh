@@ -131,7 +131,8 @@ struct StageArgs {
     T* k1_th; T* k1_ph;
     T* k3_th; T* k3_ph;
     T* k4_th; T* k4_ph;
-    T* y32_th; T* y32_ph;    // binary32 form of the full model: binary32 copy of the state (stage 1 writes it)
+    T* y32_th[2];            // binary32 form of the full model: binary32 copies of the state buffers (set with
+    T* y32_ph[2];            // the state; stage 5 writes that of the candidate state beside it)
     const T* G;              // glass field
     // full model, binary64: per-cell coefficients precomputed from G (SoA, NSTATIC arrays of n cells):
     // [0] A_lam [1] B_lam (lambda' = A + B phi)  [2] W = 2 I_W/(alpha xi^2) before the max

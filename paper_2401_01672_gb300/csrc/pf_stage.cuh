@@ -34,7 +34,8 @@
 // u5 = u4 + 3dt/8 k1 - 15dt/8 k3 + 2dt k4 -- algebraically the tableau rows) so that
 // only stages 1 and 5 touch the binary64 state; the state update y' = y + (dt/6 (k1 +
 // 4k4 + k5)) adds a binary32 increment to binary64 y.  For the full model the chained quantities are
-// the increments d_s = u_s - y32 over a binary32 copy y32 of the state (written by stage 1), and the
+// the increments d_s = u_s - y32 over a binary32 copy y32 of the state (set with the state, written by
+// stage 5 beside the candidate state, so stage 1 reads it instead of the binary64 state), and the
 // stiff terms (heat flux, Laplacian) are formed from differences of y32 and of d_s separately: the
 // rounding of y to binary32 is then the same in every stage and drops out of the error estimate
 // (2 - 9 + 8 - 1 = 0), where rounding each u_s separately left a noise floor in E that the latent
@@ -318,8 +319,10 @@ __device__ __forceinline__ void publish_block(Ctrl* ctrl, unsigned long long ebi
 // persistent kernel (blocks loop over the tiles of all active instances).
 template <int MODEL, int RX, typename T, typename TIN, int STAGE, int BY>
 __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi, const int byi, const int bzi) {
-    static_assert(STAGE == 1 ? std::is_same<TIN, double>::value : std::is_same<TIN, T>::value,
-                  "stage 1 reads the binary64 state; other stages read stage buffers");
+    static_assert((STAGE == 1 && !(std::is_same<T, float>::value && MODEL == M_FULL))
+                      ? std::is_same<TIN, double>::value : std::is_same<TIN, T>::value,
+                  "stage 1 reads the binary64 state (the binary32 form of the full model: its binary32 copy); "
+                  "other stages read stage buffers");
     constexpr bool HAS_TH = (MODEL != M_MICRO);  // theta integrated
     constexpr bool HAS_PH = (MODEL != M_TEMP);   // phi integrated
     constexpr bool F32 = std::is_same<T, float>::value;
@@ -327,8 +330,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
     // full model in binary64: blends from precomputed per-cell coefficients (fewer binary64 operations)
     constexpr bool STATIC = (!F32 && MODEL == M_FULL);
     // full model in binary32: the inputs of stages 2-5 are increments d = u - y32 over the binary32 copy
-    // y32 of the state that stage 1 writes; the heat flux, the Laplacian and phi (1 - phi) take the
-    // differences of y32 and of d separately (see allen_cahn_rate_inc)
+    // y32 of the state (stage 1 reads it as its input); the heat flux, the Laplacian and phi (1 - phi)
+    // take the differences of y32 and of d separately (see allen_cahn_rate_inc)
     constexpr bool INC = (F32 && MODEL == M_FULL);
     constexpr bool DIN = (INC && STAGE >= 2);
 
@@ -386,6 +389,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
     if constexpr (STAGE == 0) {
         in_th = reinterpret_cast<const TIN*>(a.in_th);
         in_ph = reinterpret_cast<const TIN*>(a.in_ph);
+    } else if constexpr (STAGE == 1 && INC) {
+        in_th = reinterpret_cast<const TIN*>(a.y32_th[cur]);
+        in_ph = reinterpret_cast<const TIN*>(a.y32_ph[cur]);
     } else if constexpr (STAGE == 1) {
         in_th = reinterpret_cast<const TIN*>(a.y_th[cur]);
         in_ph = reinterpret_cast<const TIN*>(a.y_ph[cur]);
@@ -402,8 +408,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
     if constexpr (DIN) {
         in_dth = reinterpret_cast<const T*>(in_th);
         in_dph = reinterpret_cast<const T*>(in_ph);
-        in_th = reinterpret_cast<const TIN*>(a.y32_th);
-        in_ph = reinterpret_cast<const TIN*>(a.y32_ph);
+        in_th = reinterpret_cast<const TIN*>(a.y32_th[cur]);
+        in_ph = reinterpret_cast<const TIN*>(a.y32_ph[cur]);
     }
     const T* __restrict__ Gf = a.G;
 
@@ -814,8 +820,6 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
                 if (a.out_ph) a.out_ph[id] = dph;
             } else if constexpr (STAGE == 1) {
                 if constexpr (INC) {
-                    a.y32_th[id] = thc;
-                    a.y32_ph[id] = phc;
                     a.k1_th[id] = dth;
                     a.ua_th[id] = sc[0] * dth;
                     a.k1_ph[id] = dph;
@@ -864,13 +868,21 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& a, const int bxi,
                 // |2k1 - 9k3 + 8k4 - k5| here; the factor dt/30 is applied to the block maximum
                 // (rounding is monotone, so max(dt/30 |x|) = dt/30 max |x| exactly)
                 if constexpr (HAS_TH) {
-                    if constexpr (F32) a.yo_th[cur ^ 1][id] = y_t64 + widen(sc[1] * (k1t + FMA(T(4), k4t, dth)));
+                    if constexpr (F32) {
+                        const double yn = y_t64 + widen(sc[1] * (k1t + FMA(T(4), k4t, dth)));
+                        a.yo_th[cur ^ 1][id] = yn;
+                        if constexpr (INC) a.y32_th[cur ^ 1][id] = narrow(yn);
+                    }
                     else a.yo_th[cur ^ 1][id] = FMA(sc[1], k1t + FMA(T(4), k4t, dth), y_t64);
                     const unsigned long long eb = abs_bits(FMA(T(2), k1t, FMA(T(-9), k3t, FMA(T(8), k4t, -dth))));
                     ebits = eb > ebits ? eb : ebits;
                 }
                 if constexpr (HAS_PH) {
-                    if constexpr (F32) a.yo_ph[cur ^ 1][id] = y_p64 + widen(sc[1] * (k1p + FMA(T(4), k4p, dph)));
+                    if constexpr (F32) {
+                        const double yn = y_p64 + widen(sc[1] * (k1p + FMA(T(4), k4p, dph)));
+                        a.yo_ph[cur ^ 1][id] = yn;
+                        if constexpr (INC) a.y32_ph[cur ^ 1][id] = narrow(yn);
+                    }
                     else a.yo_ph[cur ^ 1][id] = FMA(sc[1], k1p + FMA(T(4), k4p, dph), y_p64);
                     const unsigned long long eb = abs_bits(FMA(T(2), k1p, FMA(T(-9), k3p, FMA(T(8), k4p, -dph))));
                     ebits = eb > ebits ? eb : ebits;
@@ -953,7 +965,8 @@ batch_stage_kernel_r128(const StageArgs<T>* __restrict__ args, const BatchPlan* 
 // ---------------------------------------------------------------- launchers (one per field type)
 template <typename T, int MODEL, int RX, int STAGE, int BY>
 void launch_one(const StageArgs<T>& a, dim3 grid, cudaStream_t s) {
-    using TIN = typename std::conditional<STAGE == 1, double, T>::type;
+    using TIN = typename std::conditional<STAGE == 1 && !(std::is_same<T, float>::value && MODEL == M_FULL), double,
+                                          T>::type;
     if constexpr (std::is_same<T, double>::value)
         stage_kernel_r128<MODEL, RX, T, TIN, STAGE, BY><<<grid, dim3(TX, BY), 0, s>>>(a);
     else
@@ -979,7 +992,8 @@ cudaError_t launch_by(int stage, const StageArgs<T>& a, cudaStream_t s) {
 
 template <typename T, int MODEL, int RX, int STAGE, int BY>
 void batch_one(const StageArgs<T>* args, const BatchPlan* plan, const int4* tg, int blocks, cudaStream_t s) {
-    using TIN = typename std::conditional<STAGE == 1, double, T>::type;
+    using TIN = typename std::conditional<STAGE == 1 && !(std::is_same<T, float>::value && MODEL == M_FULL), double,
+                                          T>::type;
     if constexpr (std::is_same<T, double>::value)
         batch_stage_kernel_r128<MODEL, RX, T, TIN, STAGE, BY><<<blocks, dim3(TX, BY), 0, s>>>(args, plan, tg);
     else
