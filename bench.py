@@ -57,11 +57,11 @@ FLOPS_RHS = 64
 FLOPS_COMB = [4, 6, 8, 12, 24]
 # DRAM traffic per cell of the stage-5 kernels from one ncu capture each at 192^3, mid-front state
 # (dram__bytes_read.sum + dram__bytes_write.sum over 7,077,888 cells; None once a kernel changes until
-# it is captured again).  Binary64: 1027.7 MB -- the method's 104 B plus the per-cell blend
+# it is captured again).  Binary64: 1072.2 MB -- the method's 104 B plus the per-cell blend
 # coefficients (64 B where the Allen-Cahn arithmetic runs, 24 B in the bulk), read instead of
 # recomputed on the binary64 pipe that bounds it.  Binary32 form (increments over a binary32 copy of the
 # state, which stage 5 writes): 585.6 MB, the method's 84 B.
-TRAFFIC_F64_S5_PER_CELL = 145.2
+TRAFFIC_F64_S5_PER_CELL = 151.5
 TRAFFIC_F32_S5_PER_CELL = 82.7
 KERNEL_BYTES_F64_S5 = None
 

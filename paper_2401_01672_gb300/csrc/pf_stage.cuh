@@ -922,11 +922,15 @@ stage_kernel(const StageArgs<T> a) {
     stage_tile<MODEL, RX, T, TIN, STAGE, BY>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-// Binary64 form: at most 128 registers per thread, so that 16 warps of every block shape stay resident
-// on an SM (measured faster than one 8-warp block at 136 registers).  The binary32 kernels keep the
-// compiler's own register choice (an explicit bound, even of one block, made it take more registers).
+// Binary64 form: resident blocks per SM the register bound is set for.  Blocks of 32 x 4: six (24 warps,
+// at most 85 registers per thread; measured 2.3 % faster over the five stages at 256^3 than 16 warps at
+// 128 registers, 28 and 32 warps slower); 32 x 8 and 32 x 16: 16 warps at 128 registers (measured
+// faster than one 8-warp block at 136 registers).  The binary32 kernels keep the compiler's own
+// register choice (an explicit bound, even of one block, made it take more registers).
+constexpr int f64_min_blocks(int by) { return by == 4 ? 6 : 16 / by; }
+
 template <int MODEL, int RX, typename T, typename TIN, int STAGE, int BY>
-__global__ void __launch_bounds__(TX * BY, 16 / BY)
+__global__ void __launch_bounds__(TX * BY, f64_min_blocks(BY))
 stage_kernel_r128(const StageArgs<T> a) {
     stage_tile<MODEL, RX, T, TIN, STAGE, BY>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
@@ -956,7 +960,7 @@ batch_stage_kernel(const StageArgs<T>* __restrict__ args, const BatchPlan* __res
 }
 
 template <int MODEL, int RX, typename T, typename TIN, int STAGE, int BY>
-__global__ void __launch_bounds__(TX * BY, 16 / BY)
+__global__ void __launch_bounds__(TX * BY, f64_min_blocks(BY))
 batch_stage_kernel_r128(const StageArgs<T>* __restrict__ args, const BatchPlan* __restrict__ plan,
                         const int4* __restrict__ tilegrid) {
     batch_tiles<MODEL, RX, T, TIN, STAGE, BY>(args, plan, tilegrid);
