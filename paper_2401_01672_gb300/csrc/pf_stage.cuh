@@ -922,12 +922,13 @@ stage_kernel(const StageArgs<T> a) {
     stage_tile<MODEL, RX, T, TIN, STAGE, BY>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-// Binary64 form: resident blocks per SM the register bound is set for.  Blocks of 32 x 4: six (24 warps,
-// at most 85 registers per thread; measured 2.3 % faster over the five stages at 256^3 than 16 warps at
-// 128 registers, 28 and 32 warps slower); 32 x 8 and 32 x 16: 16 warps at 128 registers (measured
-// faster than one 8-warp block at 136 registers).  The binary32 kernels keep the compiler's own
-// register choice (an explicit bound, even of one block, made it take more registers).
-constexpr int f64_min_blocks(int by) { return by == 4 ? 6 : 16 / by; }
+// Binary64 form: resident blocks per SM the register bound is set for: 24 warps for blocks of 32 x 4 and
+// 32 x 8 (at most 85 registers per thread, some spilled; measured over the five stages at 256^3: 2.3 %
+// faster than 16 warps at 128 registers with 32 x 4, 3.5 % with 32 x 8; 28 and 32 warps slower), one
+// block of 32 x 16 (16 warps at 128 registers; one 8-warp block at 136 registers was slower).  The
+// binary32 kernels keep the compiler's own register choice (an explicit bound, even of one block, made
+// it take more registers).
+constexpr int f64_min_blocks(int by) { return by <= 8 ? 24 / by : 1; }
 
 template <int MODEL, int RX, typename T, typename TIN, int STAGE, int BY>
 __global__ void __launch_bounds__(TX * BY, f64_min_blocks(BY))
